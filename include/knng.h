@@ -1,0 +1,194 @@
+/*
+ * knng.h -- C ABI of the GB300 (sm_103a) NN-Descent K-nearest-neighbour graph
+ * library for the squared l2 metric.
+ *
+ * The method is NN-Descent as optimised in "Fast single-core K-Nearest
+ * Neighbor Graph computation" (Kluser, Bokstaller, Rutz, Buner): random
+ * initialisation (Section 2), one-pass probability sampling of forward and
+ * reverse neighbours (Section 3.1), the local join that evaluates squared l2
+ * distances between candidate pairs and updates both endpoints' lists
+ * (Section 2, Section 3.3), termination on the number of changes (Section 2)
+ * and the greedy clustering relabelling (Section 3.2, Algorithm 1).  Every
+ * step runs in CUDA kernels; this header is the only boundary.
+ *
+ * Conventions shared by every call
+ *   - Points: `data` is n x d float32, row-major, contiguous (row stride d).
+ *     It may be a host pointer or a device pointer of the current device; the
+ *     library tells them apart with cudaPointerGetAttributes.  Host inputs are
+ *     copied to the device; host outputs are filled by a device-to-host copy.
+ *   - Output graph: ids[u*K + j] (int32) and dists[u*K + j] (float32 squared
+ *     l2) hold u's j-th nearest neighbour found; each row is ascending by
+ *     (dist, id), holds no self-loop and no repeated id.
+ *   - Ownership: the caller owns data, ids, dists and every other pointer it
+ *     passes; the library never frees them.  A knng_ctx owns all device
+ *     memory it allocates and frees it in knng_destroy.
+ *   - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *     All work is enqueued on it.  Calls that return device-computed numbers
+ *     to the host (knng_iterate's change count, host outputs) synchronise that
+ *     stream only, never the whole device.
+ *   - Errors: every call returns KNNG_OK (0), a negative KNNG_ERR_* code, or
+ *     the positive warning KNNG_WARN_OVERFLOW (result valid, but some sampled
+ *     candidates did not fit their fixed capacity and were skipped).  No C++
+ *     exception crosses this boundary.  knng_strerror names a code.
+ *   - Limits: 2 <= n < 2^30 - 1, 1 <= d, 1 <= K <= min(32, n - 1),
+ *     0 < rho <= 1, delta >= 0, 0 <= max_iters <= 1000.
+ */
+#ifndef KNNG_H_
+#define KNNG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KNNG_OK 0
+#define KNNG_WARN_OVERFLOW 1
+#define KNNG_ERR_INVALID_ARG (-1)
+#define KNNG_ERR_OOM (-2)
+#define KNNG_ERR_CUDA (-3)
+#define KNNG_ERR_TIMEOUT (-4)
+#define KNNG_ERR_UNSUPPORTED (-5)
+#define KNNG_ERR_STATE (-6)
+#define KNNG_ERR_INTERNAL (-7)
+
+/* flags for knng_init / knng_build_ex */
+#define KNNG_FLAG_REORDER 0x1u   /* Algorithm 1 (list of the node on spot i) + relabel after iteration 1 */
+#define KNNG_FLAG_REORDER_B 0x2u /* with REORDER: the literal reading (list of node i) */
+#define KNNG_FLAG_TIMING 0x4u    /* record CUDA events around every local-join launch */
+#define KNNG_FLAG_GRAPH 0x8u     /* knng_run: replay the iteration loop as one CUDA graph */
+
+typedef struct knng_ctx knng_ctx;
+
+/* Counters read back by knng_get_stats.  Work counters add up over all
+ * iterations run so far. */
+typedef struct knng_stats {
+    int64_t n;
+    int32_t d, K, s;           /* s = ceil(rho * K), the sample size per kind */
+    int32_t iterations;        /* iterations that ran (converged ones skip) */
+    int64_t dist_evals;        /* local-join distance evaluations */
+    int64_t last_changes;      /* list entries new after the last iteration run */
+    int64_t inserts;           /* successful list insertions (incl. later evicted) */
+    int64_t merges;            /* locked list merges */
+    int64_t gathered_rows;     /* candidate rows read by the local join */
+    int64_t rev_overflow;      /* reverse candidates skipped (capacity R per kind) */
+    int64_t set_overflow;      /* candidates skipped beyond 64 per node and iteration */
+    int64_t lock_timeouts;     /* bounded lock waits that gave up (then KNNG_ERR_TIMEOUT) */
+    int64_t kernel_launches;   /* kernels this context launched */
+    int32_t reordered;         /* 1 once Algorithm 1 relabelled the points */
+    int32_t join_launches;     /* local-join launches timed (KNNG_FLAG_TIMING) */
+    double join_ms;            /* their summed CUDA-event time */
+} knng_stats;
+
+/*
+ * One-shot K-NNG build (Section 2): random init, then up to max_iters
+ * iterations of selection + calculation, stopping after the first iteration
+ * whose change count is below delta * n * K; the final lists are re-ranked
+ * with direct float32 difference-form distances.  rho sets the sample size
+ * s = ceil(rho * K) (Section 3.1).  seed drives every random choice through a
+ * counter-based SplitMix64 hash, so a build is reproducible.  Uses the legacy
+ * default stream and no flags; returns when ids/dists are written.
+ */
+int knng_build(const float *data, int64_t n, int d, int K, float rho, float delta,
+               int max_iters, uint64_t seed, int32_t *ids, float *dists);
+
+/* knng_build with flags (KNNG_FLAG_*), a stream and optional statistics
+ * (stats may be NULL).  With device outputs the call does not wait for the
+ * results beyond what reading stats needs. */
+int knng_build_ex(const float *data, int64_t n, int d, int K, float rho, float delta,
+                  int max_iters, uint64_t seed, uint32_t flags, void *stream,
+                  int32_t *ids, float *dists, knng_stats *stats);
+
+/*
+ * Create a context and run the random initialisation (Section 2: K distinct
+ * neighbours != u per point, uniform over V).  Allocates all device memory
+ * the build needs.  *out is NULL on error.
+ */
+int knng_init(knng_ctx **out, const float *data, int64_t n, int d, int K, float rho,
+              float delta, uint64_t seed, uint32_t flags, void *stream);
+
+/*
+ * Create a context whose starting graph is given: ids (n x K, each row K
+ * distinct ids != u) and is_new (n x K bytes, nonzero = "new" flag).  Lists
+ * are sorted and their distances computed on the device.  `iter` is the
+ * number of iterations already done (the next knng_iterate runs iter + 1, which
+ * selects the random stream).  For resuming a build and for step-level tests.
+ */
+int knng_init_from_graph(knng_ctx **out, const float *data, int64_t n, int d, int K,
+                         float rho, float delta, uint64_t seed, uint32_t flags, void *stream,
+                         const int32_t *ids, const uint8_t *is_new, int iter);
+
+/*
+ * One NN-Descent iteration (Section 2): degree counting and one-pass sampling
+ * (Section 3.1), then the local join with list updates (Sections 2, 3.3).
+ * With KNNG_FLAG_REORDER, the first iteration is followed by Algorithm 1 and
+ * the relabelling (Section 3.2).  Synchronises the stream and writes the
+ * iteration's change count to *changes_out (may be NULL).  Returns 1 when the
+ * count is below delta * n * K (converged), 0 otherwise, or an error.
+ */
+int knng_iterate(knng_ctx *ctx, int64_t *changes_out);
+
+/*
+ * Enqueue up to max_iters iterations without host round trips: each iteration's
+ * kernels skip themselves on the device once a previous iteration's change count
+ * fell below delta * n * K.  Does not synchronise.
+ */
+int knng_run(knng_ctx *ctx, int max_iters);
+
+/* Algorithm 1 on the current lists (the node on spot i, or node i with
+ * KNNG_FLAG_REORDER_B) and the relabelling of points and lists (Section 3.2).
+ * Normally run by knng_iterate after the first iteration. */
+int knng_reorder(knng_ctx *ctx);
+
+/*
+ * Final graph in the caller's labelling: every entry's distance recomputed in
+ * float32 difference form, rows sorted by (dist, original id).  ids/dists are
+ * n x K, host or device.
+ */
+int knng_get(knng_ctx *ctx, int32_t *ids, float *dists);
+
+/*
+ * Raw current state in the current (possibly relabelled) labelling: ids, list
+ * distances, flags (bit 0 = new).  Any pointer may be NULL.  Host pointers.
+ */
+int knng_get_state(knng_ctx *ctx, int32_t *ids, float *dists, uint8_t *flags);
+
+/*
+ * Candidate sets of the last iteration's selection step, after repeats were
+ * removed, in the current labelling: new_ids / old_ids are n x cap (host),
+ * unused slots -1, counts in new_cnt / old_cnt.  Order within a set is not
+ * specified.  Sets are kept until the next iteration.  For tests.
+ */
+int knng_get_samples(knng_ctx *ctx, int cap, int32_t *new_ids, int32_t *new_cnt,
+                     int32_t *old_ids, int32_t *old_cnt);
+
+/* sigma (n, host): the spot of each original point; identity until reordered. */
+int knng_get_permutation(knng_ctx *ctx, int32_t *sigma);
+
+/* Counters; synchronises the stream. */
+int knng_get_stats(knng_ctx *ctx, knng_stats *stats);
+
+/* Free a context and its device memory (stream-ordered).  NULL is fine. */
+int knng_destroy(knng_ctx *ctx);
+
+/*
+ * Exact K-NNG by brute force (Section 2: every distance, the K smallest per
+ * point by (dist, id), float32 difference-form distances).  rows (host or
+ * device int64, may be NULL = all n rows) selects nq query points; outputs
+ * are nq x K.  Ground truth for recall.
+ */
+int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *rows,
+                    int64_t nq, int32_t *ids, float *dists, void *stream);
+
+/* Name of a return code. */
+const char *knng_strerror(int code);
+
+/* Library version string. */
+const char *knng_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNNG_H_ */

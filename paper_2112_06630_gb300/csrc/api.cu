@@ -1,0 +1,588 @@
+// api.cu -- the C ABI (include/knng.h): argument checks, the context and its
+// device memory, and the order in which the kernels of an NN-Descent build are
+// enqueued.  No computation of the method happens here; every step is a
+// kernel launch on the caller's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/knng.h"
+#include "internal.h"
+
+using namespace knng;
+
+namespace {
+
+constexpr int kMaxLocalIters = 1024;
+constexpr int kMaxItersArg = 1000;
+
+int rev_capacity(int s) { return 2 * s + 8; }
+
+int sample_size(float rho, int K) {
+    int s = (int)std::ceil((double)rho * (double)K - 1e-9);
+    if (s < 1) s = 1;
+    if (s > K) s = K;
+    return s;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int cuda_code(cudaError_t e) { return e == cudaSuccess ? KNNG_OK : (e == cudaErrorMemoryAllocation ? KNNG_ERR_OOM : KNNG_ERR_CUDA); }
+
+#define KNNG_TRY(expr)                              \
+    do {                                            \
+        cudaError_t _e = (expr);                    \
+        if (_e != cudaSuccess) return cuda_code(_e); \
+    } while (0)
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int check_args(int64_t n, int d, int K, float rho, float delta) {
+    if (n < 2 || n >= (int64_t(1) << 30) - 1) return KNNG_ERR_INVALID_ARG;
+    if (d < 1 || K < 1 || K > n - 1) return KNNG_ERR_INVALID_ARG;
+    if (!(rho > 0.0f && rho <= 1.0f) || !(delta >= 0.0f)) return KNNG_ERR_INVALID_ARG;
+    if (K > kMaxK) return KNNG_ERR_UNSUPPORTED;
+    return KNNG_OK;
+}
+
+}  // namespace
+
+struct knng_ctx {
+    int64_t n = 0;
+    int d = 0, dp = 0, nv = 0, K = 0, s = 0, R = 0, cap = 0;
+    float rho = 0, delta = 0;
+    uint64_t seed = 0;
+    uint32_t flags = 0;
+    cudaStream_t stream = nullptr;
+    double thr = 0;
+    int it_done = 0;    // absolute iterations done (selects the random streams)
+    int li = 0;         // iterations launched by this context
+    bool reordered = false;
+    long long launches = 0;
+
+    unsigned char *arena = nullptr;
+    float *X = nullptr, *X2 = nullptr;
+    uint64_t *keys = nullptr, *keys2 = nullptr;
+    int *locks = nullptr, *ibuf = nullptr, *cand = nullptr, *err = nullptr;
+    int32_t *sigma = nullptr, *sigma_inv = nullptr, *total_perm = nullptr, *total_inv = nullptr;
+    long long *stats = nullptr, *it_stats = nullptr;
+
+    std::vector<cudaEvent_t> ev;  // start/stop pairs around join launches
+    int timed = 0;
+
+    DevState dev(bool gate) const {
+        DevState st;
+        st.X = X;
+        st.keys = keys;
+        st.locks = locks;
+        st.rev_new = ibuf;
+        st.rev_old = ibuf + n;
+        st.fill_new = ibuf + 2 * n;
+        st.fill_old = ibuf + 3 * n;
+        st.fwd_new = ibuf + 4 * n;
+        st.fwd_old = ibuf + 5 * n;
+        st.cand_new = cand;
+        st.cand_old = cand + (size_t)n * cap;
+        st.stats = stats;
+        st.it_stats = it_stats;
+        st.n = n;
+        st.dp = dp;
+        st.nv = nv;
+        st.K = K;
+        st.s = s;
+        st.R = R;
+        st.cap = cap;
+        st.thr = gate ? thr : -1.0;
+        return st;
+    }
+};
+
+namespace {
+
+int ctx_alloc(knng_ctx *c) {
+    const int64_t n = c->n;
+    const bool reorder = (c->flags & KNNG_FLAG_REORDER) != 0;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    const size_t oX = take(sizeof(float) * n * c->dp);
+    const size_t oX2 = reorder ? take(sizeof(float) * n * c->dp) : 0;
+    const size_t oK = take(sizeof(uint64_t) * n * c->K);
+    const size_t oK2 = reorder ? take(sizeof(uint64_t) * n * c->K) : 0;
+    const size_t oL = take(sizeof(int) * n);
+    const size_t oI = take(sizeof(int) * 6 * n);
+    const size_t oC = take(sizeof(int) * 2 * (size_t)n * c->cap);
+    const size_t oP = reorder ? take(sizeof(int32_t) * 4 * n) : 0;
+    const size_t oS = take(sizeof(long long) * kStatCount);
+    const size_t oT = take(sizeof(long long) * kItCount * kMaxLocalIters);
+    const size_t oE = take(sizeof(int));
+    cudaError_t e = cudaMallocAsync((void **)&c->arena, off, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_code(e);
+    }
+    unsigned char *a = c->arena;
+    c->X = (float *)(a + oX);
+    c->X2 = reorder ? (float *)(a + oX2) : nullptr;
+    c->keys = (uint64_t *)(a + oK);
+    c->keys2 = reorder ? (uint64_t *)(a + oK2) : nullptr;
+    c->locks = (int *)(a + oL);
+    c->ibuf = (int *)(a + oI);
+    c->cand = (int *)(a + oC);
+    if (reorder) {
+        int32_t *p = (int32_t *)(a + oP);
+        c->sigma = p;
+        c->sigma_inv = p + n;
+        c->total_perm = p + 2 * n;
+        c->total_inv = p + 3 * n;
+    }
+    c->stats = (long long *)(a + oS);
+    c->it_stats = (long long *)(a + oT);
+    c->err = (int *)(a + oE);
+    KNNG_TRY(cudaMemsetAsync(c->locks, 0, sizeof(int) * n, c->stream));
+    KNNG_TRY(cudaMemsetAsync(c->ibuf, 0, sizeof(int) * 6 * n, c->stream));
+    KNNG_TRY(cudaMemsetAsync(c->stats, 0, sizeof(long long) * kStatCount, c->stream));
+    KNNG_TRY(cudaMemsetAsync(c->it_stats, 0, sizeof(long long) * kItCount * kMaxLocalIters, c->stream));
+    KNNG_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    return KNNG_OK;
+}
+
+// Stage the caller's points (host or device) into the padded layout.
+int ctx_stage(knng_ctx *c, const float *data) {
+    const size_t bytes = sizeof(float) * c->n * c->d;
+    const float *src = data;
+    float *tmp = nullptr;
+    if (!is_device_ptr(data)) {
+        KNNG_TRY(cudaMallocAsync((void **)&tmp, bytes, c->stream));
+        KNNG_TRY(cudaMemcpyAsync(tmp, data, bytes, cudaMemcpyHostToDevice, c->stream));
+        src = tmp;
+    }
+    KNNG_TRY(launch_stage(src, c->n, c->d, c->X, c->dp, c->stream));
+    c->launches++;
+    if (tmp) KNNG_TRY(cudaFreeAsync(tmp, c->stream));
+    return KNNG_OK;
+}
+
+int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float rho, float delta, uint64_t seed,
+               uint32_t flags, void *stream) {
+    if (!out) return KNNG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!data) return KNNG_ERR_INVALID_ARG;
+    int rc = check_args(n, d, K, rho, delta);
+    if (rc) return rc;
+    knng_ctx *c = new (std::nothrow) knng_ctx();
+    if (!c) return KNNG_ERR_OOM;
+    c->n = n;
+    c->d = d;
+    c->dp = (d + 3) & ~3;
+    c->nv = c->dp / 4;
+    c->K = K;
+    c->s = sample_size(rho, K);
+    c->R = rev_capacity(c->s);
+    c->cap = K + c->R;
+    c->rho = rho;
+    c->delta = delta;
+    c->seed = seed;
+    c->flags = flags;
+    c->stream = (cudaStream_t)stream;
+    c->thr = (double)delta * (double)n * (double)K;
+    rc = ctx_alloc(c);
+    if (!rc) rc = ctx_stage(c, data);
+    if (!rc && c->total_perm) {
+        // the relabelling original -> spot starts as the identity
+        rc = cuda_code(launch_iota(c->total_perm, c->n, c->stream));
+        c->launches++;
+    }
+    if (rc) {
+        knng_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return KNNG_OK;
+}
+
+// Read the device error word and lock-timeout counter (synchronises the stream).
+int ctx_check(knng_ctx *c) {
+    int err = 0;
+    long long st[kStatCount];
+    KNNG_TRY(cudaMemcpyAsync(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    KNNG_TRY(cudaMemcpyAsync(st, c->stats, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    KNNG_TRY(cudaStreamSynchronize(c->stream));
+    KNNG_TRY(cudaGetLastError());
+    if (err & 2) return KNNG_ERR_INVALID_ARG;
+    if (err) return KNNG_ERR_INTERNAL;
+    if (st[kStatLockTimeout]) return KNNG_ERR_TIMEOUT;
+    if (st[kStatRevOverflow] || st[kStatSetOverflow]) return KNNG_WARN_OVERFLOW;
+    return KNNG_OK;
+}
+
+int enqueue_reorder(knng_ctx *c) {
+    if (!c->sigma) return KNNG_ERR_STATE;
+    const int reading_b = (c->flags & KNNG_FLAG_REORDER_B) ? 1 : 0;
+    KNNG_TRY(launch_greedy_reorder(c->keys, c->n, c->K, reading_b, c->sigma, c->sigma_inv, c->stream));
+    DevState st = c->dev(false);
+    KNNG_TRY(launch_permute(st, c->X2, c->keys2, c->sigma, c->total_perm, c->stream));
+    c->launches += 2;
+    std::swap(c->X, c->X2);
+    std::swap(c->keys, c->keys2);
+    c->reordered = true;
+    return KNNG_OK;
+}
+
+// One iteration: count, sample, join (+ Algorithm 1 after the first one).
+int enqueue_iteration(knng_ctx *c, bool gate) {
+    if (c->li >= kMaxLocalIters) return KNNG_ERR_STATE;
+    const int li = c->li, it = c->it_done + 1;
+    DevState st = c->dev(gate);
+    KNNG_TRY(launch_count(st, li, c->stream));
+    KNNG_TRY(launch_sample(st, li, it, c->seed, c->stream));
+    const bool timing = (c->flags & KNNG_FLAG_TIMING) != 0;
+    if (timing) {
+        cudaEvent_t a, b;
+        KNNG_TRY(cudaEventCreate(&a));
+        KNNG_TRY(cudaEventCreate(&b));
+        c->ev.push_back(a);
+        c->ev.push_back(b);
+        KNNG_TRY(cudaEventRecord(a, c->stream));
+    }
+    KNNG_TRY(launch_join(st, li, c->stream));
+    if (timing) KNNG_TRY(cudaEventRecord(c->ev.back(), c->stream));
+    c->launches += 3;
+    c->li++;
+    c->it_done++;
+    if ((c->flags & KNNG_FLAG_REORDER) && !c->reordered && it == 1) {
+        int rc = enqueue_reorder(c);
+        if (rc) return rc;
+    }
+    return KNNG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *knng_strerror(int code) {
+    switch (code) {
+        case KNNG_OK: return "ok";
+        case KNNG_WARN_OVERFLOW: return "warning: sampled candidates beyond capacity were skipped";
+        case KNNG_ERR_INVALID_ARG: return "invalid argument";
+        case KNNG_ERR_OOM: return "out of device memory";
+        case KNNG_ERR_CUDA: return "CUDA error";
+        case KNNG_ERR_TIMEOUT: return "a bounded device wait gave up";
+        case KNNG_ERR_UNSUPPORTED: return "unsupported parameters (K > 32)";
+        case KNNG_ERR_STATE: return "call not valid in the context's state";
+        case KNNG_ERR_INTERNAL: return "internal error";
+        default: return "unknown code";
+    }
+}
+
+const char *knng_version(void) { return "knng-gb300 0.1 (sm_103a)"; }
+
+int knng_init(knng_ctx **out, const float *data, int64_t n, int d, int K, float rho, float delta, uint64_t seed,
+              uint32_t flags, void *stream) {
+    int rc = ctx_create(out, data, n, d, K, rho, delta, seed, flags, stream);
+    if (rc) return rc;
+    knng_ctx *c = *out;
+    DevState st = c->dev(false);
+    cudaError_t e = launch_init_random(st, seed, c->err, c->stream);
+    c->launches++;
+    if (e != cudaSuccess) {
+        knng_destroy(c);
+        *out = nullptr;
+        return cuda_code(e);
+    }
+    return KNNG_OK;
+}
+
+int knng_init_from_graph(knng_ctx **out, const float *data, int64_t n, int d, int K, float rho, float delta,
+                         uint64_t seed, uint32_t flags, void *stream, const int32_t *ids, const uint8_t *is_new,
+                         int iter) {
+    if (!ids || !is_new || iter < 0) return KNNG_ERR_INVALID_ARG;
+    int rc = ctx_create(out, data, n, d, K, rho, delta, seed, flags, stream);
+    if (rc) return rc;
+    knng_ctx *c = *out;
+    c->it_done = iter;
+    int32_t *dids = nullptr;
+    uint8_t *dnew = nullptr;
+    const size_t nb = sizeof(int32_t) * n * K, fb = (size_t)n * K;
+    cudaError_t e = cudaSuccess;
+    const int32_t *ids_d = ids;
+    const uint8_t *new_d = is_new;
+    if (!is_device_ptr(ids)) {
+        e = cudaMallocAsync((void **)&dids, nb, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dids, ids, nb, cudaMemcpyHostToDevice, c->stream);
+        ids_d = dids;
+    }
+    if (e == cudaSuccess && !is_device_ptr(is_new)) {
+        e = cudaMallocAsync((void **)&dnew, fb, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dnew, is_new, fb, cudaMemcpyHostToDevice, c->stream);
+        new_d = dnew;
+    }
+    if (e == cudaSuccess) {
+        e = launch_init_graph(c->dev(false), ids_d, new_d, c->err, c->stream);
+        c->launches++;
+    }
+    if (dids) cudaFreeAsync(dids, c->stream);
+    if (dnew) cudaFreeAsync(dnew, c->stream);
+    if (e == cudaSuccess) {
+        rc = ctx_check(c);
+        if (rc == KNNG_ERR_INVALID_ARG || rc < 0) {
+            knng_destroy(c);
+            *out = nullptr;
+            return rc;
+        }
+        return KNNG_OK;
+    }
+    knng_destroy(c);
+    *out = nullptr;
+    return cuda_code(e);
+}
+
+int knng_iterate(knng_ctx *c, int64_t *changes_out) {
+    if (!c) return KNNG_ERR_INVALID_ARG;
+    const int li = c->li;
+    int rc = enqueue_iteration(c, false);
+    if (rc) return rc;
+    long long its[kItCount];
+    KNNG_TRY(cudaMemcpyAsync(its, c->it_stats + (size_t)li * kItCount, sizeof(its), cudaMemcpyDeviceToHost,
+                             c->stream));
+    rc = ctx_check(c);
+    if (rc < 0) return rc;
+    if (changes_out) *changes_out = its[kItChanges];
+    return (double)its[kItChanges] < c->thr ? 1 : 0;
+}
+
+int knng_run(knng_ctx *c, int max_iters) {
+    if (!c || max_iters < 0 || max_iters > kMaxItersArg) return KNNG_ERR_INVALID_ARG;
+    for (int t = 0; t < max_iters; ++t) {
+        int rc = enqueue_iteration(c, true);
+        if (rc) return rc;
+    }
+    return KNNG_OK;
+}
+
+int knng_reorder(knng_ctx *c) {
+    if (!c) return KNNG_ERR_INVALID_ARG;
+    return enqueue_reorder(c);
+}
+
+int knng_get(knng_ctx *c, int32_t *ids, float *dists) {
+    if (!c || !ids || !dists) return KNNG_ERR_INVALID_ARG;
+    const bool dev_out = is_device_ptr(ids) && is_device_ptr(dists);
+    const size_t ib = sizeof(int32_t) * c->n * c->K, db = sizeof(float) * c->n * c->K;
+    int32_t *oi = ids;
+    float *od = dists;
+    unsigned char *tmp = nullptr;
+    if (!dev_out) {
+        KNNG_TRY(cudaMallocAsync((void **)&tmp, align256(ib) + db, c->stream));
+        oi = (int32_t *)tmp;
+        od = (float *)(tmp + align256(ib));
+    }
+    if (c->reordered) {
+        KNNG_TRY(launch_invert(c->total_perm, c->n, c->total_inv, c->stream));
+        c->launches++;
+    }
+    DevState st = c->dev(false);
+    KNNG_TRY(launch_output(st, c->reordered ? c->total_perm : nullptr, c->reordered ? c->total_inv : nullptr, oi,
+                           od, c->stream));
+    c->launches++;
+    if (!dev_out) {
+        KNNG_TRY(cudaMemcpyAsync(ids, oi, ib, cudaMemcpyDeviceToHost, c->stream));
+        KNNG_TRY(cudaMemcpyAsync(dists, od, db, cudaMemcpyDeviceToHost, c->stream));
+        KNNG_TRY(cudaFreeAsync(tmp, c->stream));
+        return ctx_check(c);
+    }
+    return KNNG_OK;
+}
+
+int knng_get_state(knng_ctx *c, int32_t *ids, float *dists, uint8_t *flags) {
+    if (!c) return KNNG_ERR_INVALID_ARG;
+    std::vector<uint64_t> k((size_t)c->n * c->K);
+    KNNG_TRY(cudaMemcpyAsync(k.data(), c->keys, sizeof(uint64_t) * k.size(), cudaMemcpyDeviceToHost, c->stream));
+    KNNG_TRY(cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < k.size(); ++i) {
+        if (ids) ids[i] = (int32_t)key_id(k[i]);
+        if (dists) {
+            uint32_t b = (uint32_t)(k[i] >> 32);
+            std::memcpy(&dists[i], &b, 4);
+        }
+        if (flags) flags[i] = (uint8_t)(key_flags(k[i]) & kFlagNew);
+    }
+    return KNNG_OK;
+}
+
+int knng_get_samples(knng_ctx *c, int cap, int32_t *new_ids, int32_t *new_cnt, int32_t *old_ids, int32_t *old_cnt) {
+    if (!c || cap < 1 || !new_ids || !new_cnt || !old_ids || !old_cnt) return KNNG_ERR_INVALID_ARG;
+    const int64_t n = c->n;
+    std::vector<int> cand((size_t)2 * n * c->cap), ib((size_t)6 * n);
+    KNNG_TRY(cudaMemcpyAsync(cand.data(), c->cand, sizeof(int) * cand.size(), cudaMemcpyDeviceToHost, c->stream));
+    KNNG_TRY(cudaMemcpyAsync(ib.data(), c->ibuf, sizeof(int) * ib.size(), cudaMemcpyDeviceToHost, c->stream));
+    KNNG_TRY(cudaStreamSynchronize(c->stream));
+    const int *fill_new = ib.data() + 2 * n, *fill_old = ib.data() + 3 * n;
+    const int *fwd_new = ib.data() + 4 * n, *fwd_old = ib.data() + 5 * n;
+    for (int64_t u = 0; u < n; ++u) {
+        for (int kind = 0; kind < 2; ++kind) {
+            const int *src = cand.data() + (size_t)kind * n * c->cap + (size_t)u * c->cap;
+            const int f = kind ? fwd_old[u] : fwd_new[u];
+            const int r = std::min(kind ? fill_old[u] : fill_new[u], c->R);
+            int32_t *dst = (kind ? old_ids : new_ids) + (size_t)u * cap;
+            int m = 0;
+            for (int i = 0; i < f && m < cap; ++i) dst[m++] = src[i];
+            for (int i = 0; i < r && m < cap; ++i) dst[m++] = src[c->K + i];
+            (kind ? old_cnt : new_cnt)[u] = m;
+            for (int i = m; i < cap; ++i) dst[i] = -1;
+        }
+    }
+    return KNNG_OK;
+}
+
+int knng_get_permutation(knng_ctx *c, int32_t *sigma) {
+    if (!c || !sigma) return KNNG_ERR_INVALID_ARG;
+    if (!c->reordered) {
+        for (int64_t u = 0; u < c->n; ++u) sigma[u] = (int32_t)u;
+        return KNNG_OK;
+    }
+    KNNG_TRY(cudaMemcpyAsync(sigma, c->total_perm, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream));
+    KNNG_TRY(cudaStreamSynchronize(c->stream));
+    return KNNG_OK;
+}
+
+int knng_get_stats(knng_ctx *c, knng_stats *out) {
+    if (!c || !out) return KNNG_ERR_INVALID_ARG;
+    long long st[kStatCount];
+    std::vector<long long> its((size_t)kItCount * std::max(1, c->li));
+    KNNG_TRY(cudaMemcpyAsync(st, c->stats, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    KNNG_TRY(cudaMemcpyAsync(its.data(), c->it_stats, sizeof(long long) * its.size(), cudaMemcpyDeviceToHost,
+                             c->stream));
+    KNNG_TRY(cudaStreamSynchronize(c->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->n = c->n;
+    out->d = c->d;
+    out->K = c->K;
+    out->s = c->s;
+    for (int i = 0; i < c->li; ++i) {
+        const long long *r = its.data() + (size_t)i * kItCount;
+        if (r[kItRan]) {
+            out->iterations++;
+            out->last_changes = r[kItChanges];
+        }
+    }
+    out->dist_evals = st[kStatEvals];
+    out->inserts = st[kStatInserts];
+    out->merges = st[kStatMerges];
+    out->gathered_rows = st[kStatGathered];
+    out->rev_overflow = st[kStatRevOverflow];
+    out->set_overflow = st[kStatSetOverflow];
+    out->lock_timeouts = st[kStatLockTimeout];
+    out->kernel_launches = c->launches;
+    out->reordered = c->reordered ? 1 : 0;
+    out->join_ms = 0;
+    for (size_t i = 0; i + 1 < c->ev.size(); i += 2) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) {
+            out->join_ms += ms;
+            out->join_launches++;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    return KNNG_OK;
+}
+
+int knng_destroy(knng_ctx *c) {
+    if (!c) return KNNG_OK;
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->arena) cudaFreeAsync(c->arena, c->stream);
+    delete c;
+    return KNNG_OK;
+}
+
+int knng_build_ex(const float *data, int64_t n, int d, int K, float rho, float delta, int max_iters, uint64_t seed,
+                  uint32_t flags, void *stream, int32_t *ids, float *dists, knng_stats *stats) {
+    if (max_iters < 0 || max_iters > kMaxItersArg || !ids || !dists) return KNNG_ERR_INVALID_ARG;
+    knng_ctx *c = nullptr;
+    int rc = knng_init(&c, data, n, d, K, rho, delta, seed, flags, stream);
+    if (rc) return rc;
+    rc = knng_run(c, max_iters);
+    if (!rc) rc = knng_get(c, ids, dists);
+    if (rc >= 0 && stats) {
+        int r2 = knng_get_stats(c, stats);
+        if (r2) rc = r2;
+    }
+    if (rc >= 0) {
+        int r3 = ctx_check(c);
+        if (r3) rc = r3;
+    }
+    knng_destroy(c);
+    return rc;
+}
+
+int knng_build(const float *data, int64_t n, int d, int K, float rho, float delta, int max_iters, uint64_t seed,
+               int32_t *ids, float *dists) {
+    return knng_build_ex(data, n, d, K, rho, delta, max_iters, seed, 0u, nullptr, ids, dists, nullptr);
+}
+
+int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *rows, int64_t nq, int32_t *ids,
+                    float *dists, void *stream) {
+    if (!data || !ids || !dists || n < 2 || d < 1 || K < 1 || K > n - 1) return KNNG_ERR_INVALID_ARG;
+    if (K > kMaxK) return KNNG_ERR_UNSUPPORTED;
+    if (!rows) nq = n;
+    if (nq < 1) return KNNG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int dp = (d + 3) & ~3;
+    const size_t xb = align256(sizeof(float) * n * dp), rb = rows ? align256(sizeof(int64_t) * nq) : 0;
+    const size_t ib = align256(sizeof(int32_t) * nq * K), db = sizeof(float) * nq * K;
+    const bool dev_out = is_device_ptr(ids) && is_device_ptr(dists);
+    unsigned char *tmp = nullptr;
+    KNNG_TRY(cudaMallocAsync((void **)&tmp, xb + rb + (dev_out ? 0 : ib + db), s));
+    float *X = (float *)tmp;
+    int rc = KNNG_OK;
+    const float *src = data;
+    float *staged = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!is_device_ptr(data)) {
+        e = cudaMallocAsync((void **)&staged, sizeof(float) * n * d, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(staged, data, sizeof(float) * n * d, cudaMemcpyHostToDevice, s);
+        src = staged;
+    }
+    if (e == cudaSuccess) e = launch_stage(src, n, d, X, dp, s);
+    const int64_t *rows_d = rows;
+    if (e == cudaSuccess && rows) {
+        if (!is_device_ptr(rows)) {
+            int64_t *r = (int64_t *)(tmp + xb);
+            e = cudaMemcpyAsync(r, rows, sizeof(int64_t) * nq, cudaMemcpyHostToDevice, s);
+            rows_d = r;
+        }
+    }
+    int32_t *oi = ids;
+    float *od = dists;
+    if (!dev_out) {
+        oi = (int32_t *)(tmp + xb + rb);
+        od = (float *)(tmp + xb + rb + ib);
+    }
+    if (e == cudaSuccess) e = launch_bruteforce(X, n, dp, K, rows_d, nq, oi, od, s);
+    if (e == cudaSuccess && !dev_out) {
+        e = cudaMemcpyAsync(ids, oi, sizeof(int32_t) * nq * K, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dists, od, db, cudaMemcpyDeviceToHost, s);
+    }
+    if (staged) cudaFreeAsync(staged, s);
+    cudaFreeAsync(tmp, s);
+    if (e == cudaSuccess && !dev_out) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_code(e);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// common.cuh -- device-side building blocks shared by the NN-Descent kernels:
+// packed list keys, the counter-based hash, the canonical float32 squared-l2
+// distance, warp sorting, and the bounded per-list lock.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace knng {
+
+// ---------------------------------------------------------------- keys ----
+// A list entry is one 64-bit key: float bits of the squared distance (high
+// word; distances are >= +0 so the bit pattern orders like the float), then
+// the neighbour id (30 bits) and two flag bits.  Ordering keys as integers
+// orders entries by (dist, id), the tie rule of the method; the flag bits sit
+// below the id and never decide an order between different ids.
+constexpr uint32_t kFlagNew = 1u;  // not yet sampled as a forward "new" candidate
+constexpr uint32_t kFlagIns = 2u;  // inserted during the current iteration
+constexpr uint64_t kKeyEmpty = ~0ull;
+constexpr int kMaxK = 32;
+
+__host__ __device__ __forceinline__ uint64_t make_key(float dist, uint32_t id, uint32_t flags) {
+#ifdef __CUDA_ARCH__
+    uint32_t bits = __float_as_uint(dist);
+#else
+    uint32_t bits;
+    __builtin_memcpy(&bits, &dist, 4);
+#endif
+    return ((uint64_t)bits << 32) | ((uint64_t)id << 2) | (uint64_t)flags;
+}
+__host__ __device__ __forceinline__ uint32_t key_id(uint64_t k) { return (uint32_t)(k >> 2) & 0x3FFFFFFFu; }
+__host__ __device__ __forceinline__ uint32_t key_flags(uint64_t k) { return (uint32_t)k & 3u; }
+__device__ __forceinline__ float key_dist(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
+// same (dist, id), flags stripped
+__host__ __device__ __forceinline__ uint64_t key_order(uint64_t k) { return k & ~3ull; }
+
+// ---------------------------------------------------------------- hash ----
+// SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).  The random
+// word for (seed, stream, iter, u, j) is mix(mix(mix(mix(seed) ^ (stream<<32 |
+// iter)) ^ u) ^ j); the first two levels depend on the launch only and are
+// computed on the host ("base").
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+enum Stream : uint32_t { kStreamInit = 1, kStreamFwd = 2, kStreamRev = 3 };
+__host__ __device__ __forceinline__ uint64_t hash_base(uint64_t seed, uint32_t stream, uint32_t iter) {
+    return splitmix64(splitmix64(seed) ^ (((uint64_t)stream << 32) | (uint64_t)iter));
+}
+__host__ __device__ __forceinline__ uint64_t hash_uj(uint64_t base, uint64_t u, uint64_t j) {
+    return splitmix64(splitmix64(base ^ u) ^ j);
+}
+// Bernoulli(s / cnt) in integers: hi32(h) * cnt < s * 2^32
+__device__ __forceinline__ bool accept(uint64_t h, uint32_t cnt, uint32_t s) {
+    return (h >> 32) * (uint64_t)cnt < ((uint64_t)s << 32);
+}
+
+// ----------------------------------------------------------- distance ----
+// Canonical float32 squared l2 (difference form, no square root): rows are
+// zero-padded to a multiple of 4 floats; four partial sums over t mod 4, each
+// accumulated in ascending t with fused multiply-add, combined as
+// (s0 + s1) + (s2 + s3).  Every float32 distance in the library (init, join,
+// brute force, re-rank) uses exactly this order, so one pair always gets one
+// value and the two orders of a pair agree bit for bit.
+struct Acc4 {
+    float s0, s1, s2, s3;
+    __device__ __forceinline__ Acc4() : s0(0.f), s1(0.f), s2(0.f), s3(0.f) {}
+    __device__ __forceinline__ void add(float4 a, float4 b) {
+        float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+        s0 = fmaf(d0, d0, s0);
+        s1 = fmaf(d1, d1, s1);
+        s2 = fmaf(d2, d2, s2);
+        s3 = fmaf(d3, d3, s3);
+    }
+    __device__ __forceinline__ float sum() const { return (s0 + s1) + (s2 + s3); }
+};
+
+__device__ __forceinline__ float l2sq_rows(const float4 *__restrict__ a, const float4 *__restrict__ b, int nv) {
+    Acc4 acc;
+    for (int v = 0; v < nv; ++v) acc.add(a[v], b[v]);
+    return acc.sum();
+}
+
+// --------------------------------------------------------------- warps ----
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
+    return __shfl_xor_sync(0xFFFFFFFFu, v, m);
+}
+
+// Ascending bitonic sort of one 64-bit key per lane across the full warp.
+__device__ __forceinline__ uint64_t warp_sort_u64(uint64_t v) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            uint64_t o = shfl_xor_u64(v, j);
+            bool up = (lane & k) == 0;
+            bool low = (lane & j) == 0;
+            uint64_t mn = v < o ? v : o, mx = v < o ? o : v;
+            v = (low == up) ? mn : mx;
+        }
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
+    return v;
+}
+
+// --------------------------------------------------------------- locks ----
+// Per-list spin lock with a bounded wait: after kLockSpinLimit failed tries
+// the caller gives up (the proposal is dropped and an error counter is
+// raised, which the host turns into KNNG_ERR_TIMEOUT).  Never waits forever.
+constexpr int kLockSpinLimit = 1 << 22;
+
+__device__ __forceinline__ bool lock_acquire(int *lock) {
+    int spins = 0;
+    while (atomicCAS(lock, 0, 1) != 0) {
+        if (++spins >= kLockSpinLimit) return false;
+        __nanosleep(spins < 64 ? 20 : 200);
+    }
+    __threadfence();
+    return true;
+}
+__device__ __forceinline__ void lock_release(int *lock) {
+    __threadfence();
+    atomicExch(lock, 0);
+}
+
+// ------------------------------------------------------------ counters ----
+// two's-complement add on a signed 64-bit counter
+__device__ __forceinline__ void atomic_add_ll(long long *p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+}
+// Global int64 counters (index into DevState::stats).
+enum Stat : int {
+    kStatEvals = 0,
+    kStatInserts,
+    kStatMerges,
+    kStatGathered,
+    kStatRevOverflow,
+    kStatSetOverflow,
+    kStatLockTimeout,
+    kStatInitAttemptsExceeded,
+    kStatCount
+};
+// Per-iteration counters (index into it_stats[iter * kItCount]).
+enum ItStat : int {
+    kItRan = 0,      // set when the iteration's join ran
+    kItChanges,      // entries inserted and still present at the end
+    kItEvals,        // distance evaluations
+    kItGathered,     // candidate rows gathered
+    kItMerges,       // locked merges
+    kItInserts,      // insertions (incl. evicted later)
+    kItCandIds,      // raw candidate ids read
+    kItCount = 8
+};
+
+struct DevState {
+    const float *X;      // n x dp, zero padded
+    uint64_t *keys;      // n x K, ascending
+    int *locks;          // n
+    int *rev_new, *rev_old;    // reverse degrees by flag
+    int *fill_new, *fill_old;  // reverse candidate fill counters
+    int *fwd_new, *fwd_old;    // accepted forward counts
+    int *cand_new, *cand_old;  // n x cap: [0, K) forward part, [K, K + R) reverse part
+    long long *stats;
+    long long *it_stats;       // (max_iters + 2) x kItCount
+    int64_t n;
+    int dp, nv, K, s, R, cap;
+    double thr;                // delta * n * K
+};
+
+// True when iteration `it` must not run because an earlier one converged.
+__device__ __forceinline__ bool iteration_skipped(const DevState &st, int it) {
+    if (it <= 1) return false;
+    const volatile long long *prev = st.it_stats + (size_t)(it - 1) * kItCount;
+    return (double)prev[kItChanges] < st.thr;
+}
+
+}  // namespace knng

@@ -1,0 +1,33 @@
+// internal.h -- host-side launchers shared between the library's translation
+// units (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace knng {
+
+// persistent grid size for a warp-per-item kernel: a multiple of the SM count
+int grid_for(const void *kernel, int block_threads, size_t dyn_smem);
+
+cudaError_t launch_stage(const float *src, int64_t n, int d, float *X, int dp, cudaStream_t s);
+cudaError_t launch_init_random(const DevState &st, uint64_t seed, int *err, cudaStream_t s);
+cudaError_t launch_init_graph(const DevState &st, const int32_t *ids, const uint8_t *is_new, int *err,
+                              cudaStream_t s);
+cudaError_t launch_count(const DevState &st, int li, cudaStream_t s);
+cudaError_t launch_sample(const DevState &st, int li, int it, uint64_t seed, cudaStream_t s);
+cudaError_t launch_join(const DevState &st, int li, cudaStream_t s);
+cudaError_t launch_greedy_reorder(const uint64_t *keys, int64_t n, int K, int reading_b, int32_t *sigma,
+                                  int32_t *sigma_inv, cudaStream_t s);
+cudaError_t launch_permute(const DevState &src, float *X_dst, uint64_t *keys_dst, const int32_t *sigma,
+                           int32_t *total_perm, cudaStream_t s);
+cudaError_t launch_output(const DevState &st, const int32_t *total_perm, const int32_t *total_inv,
+                          int32_t *ids, float *dists, cudaStream_t s);
+cudaError_t launch_iota(int32_t *p, int64_t n, cudaStream_t s);
+cudaError_t launch_invert(const int32_t *perm, int64_t n, int32_t *inv, cudaStream_t s);
+cudaError_t launch_bruteforce(const float *X, int64_t n, int dp, int K, const int64_t *rows, int64_t nq,
+                              int32_t *ids, float *dists, cudaStream_t s);
+
+}  // namespace knng

@@ -1,0 +1,367 @@
+// nnd_kernels.cu -- the NN-Descent steps around the local join: staging of
+// the points, random initialisation, degree counting, one-pass sampling, the
+// greedy relabelling (Algorithm 1) with its permutation, and the re-ranked
+// output.  One warp owns one node's list wherever a list is touched, so list
+// rows (K <= 32 keys) map onto lanes.
+#include "internal.h"
+
+namespace knng {
+
+namespace {
+constexpr int kWarpsPerBlock = 8;
+constexpr int kBlock = kWarpsPerBlock * 32;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ long long gwarp() { return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ long long nwarps() { return ((long long)gridDim.x * blockDim.x) >> 5; }
+}  // namespace
+
+int grid_for(const void *kernel, int block_threads, size_t dyn_smem) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block_threads, dyn_smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return sms * per_sm;
+}
+
+// ------------------------------------------------------------------ stage ----
+// Copy n x d rows into the padded n x dp layout (zeros in the padding), so a
+// row is a whole number of 16-byte vectors.
+__global__ void stage_kernel(const float *__restrict__ src, int64_t n, int d, float *__restrict__ X, int dp) {
+    const int64_t total = n * (int64_t)dp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t u = e / dp;
+        int t = (int)(e - u * dp);
+        X[e] = t < d ? src[u * d + t] : 0.0f;
+    }
+}
+
+cudaError_t launch_stage(const float *src, int64_t n, int d, float *X, int dp, cudaStream_t s) {
+    int grid = grid_for((const void *)stage_kernel, 256, 0);
+    stage_kernel<<<grid, 256, 0, s>>>(src, n, d, X, dp);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ random init ----
+// Section 2: K distinct neighbours != u, uniform over V.  Attempt a of node u
+// proposes v = floor(hi32(h(seed, INIT, 0, u, a)) * n / 2^32); attempts are
+// taken in order and a proposal is accepted unless it is u or already chosen.
+// A warp evaluates 32 consecutive attempts at once and accepts, in lane order,
+// exactly the proposals the sequential rule would accept.
+__global__ void __launch_bounds__(kBlock) init_random_kernel(DevState st, uint64_t base, int *err) {
+    __shared__ uint32_t chosen_s[kWarpsPerBlock][kMaxK];
+    uint32_t *chosen = chosen_s[threadIdx.x >> 5];
+    const unsigned lane = lane_id();
+    const int K = st.K;
+    const uint64_t n = (uint64_t)st.n;
+    const float4 *X4 = reinterpret_cast<const float4 *>(st.X);
+    constexpr uint64_t kMaxAttempts = 1ull << 26;
+    for (long long u = gwarp(); u < st.n; u += nwarps()) {
+        int have = 0;
+        uint64_t a = 0;
+        while (have < K) {
+            uint64_t h = hash_uj(base, (uint64_t)u, a + lane);
+            uint32_t v = (uint32_t)(((h >> 32) * n) >> 32);
+            bool ok = v != (uint32_t)u;
+            for (int k = 0; k < have; ++k) ok = ok && (chosen[k] != v);
+            unsigned same = __match_any_sync(kFull, v);
+            bool acc = ok && ((unsigned)(__ffs(same) - 1) == lane);
+            unsigned accm = __ballot_sync(kFull, acc);
+            int rank = __popc(accm & lanemask_lt());
+            __syncwarp();
+            if (acc && have + rank < K) chosen[have + rank] = v;
+            have = min(K, have + __popc(accm));
+            __syncwarp();
+            a += 32;
+            if (a >= kMaxAttempts) {
+                if (lane == 0) atomic_add_ll(&st.stats[kStatInitAttemptsExceeded], 1ll);
+                if (lane == 0) atomicOr(err, 1);
+                for (int k = have + (int)lane; k < K; k += 32) chosen[k] = (uint32_t)((u + 1 + k) % st.n);
+                have = K;
+                __syncwarp();
+            }
+        }
+        uint64_t key = kKeyEmpty;
+        if ((int)lane < K) {
+            uint32_t v = chosen[lane];
+            float dd = l2sq_rows(X4 + (size_t)u * st.nv, X4 + (size_t)v * st.nv, st.nv);
+            key = make_key(dd, v, kFlagNew);
+        }
+        key = warp_sort_u64(key);
+        if ((int)lane < K) st.keys[(size_t)u * K + lane] = key;
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_init_random(const DevState &st, uint64_t seed, int *err, cudaStream_t s) {
+    int grid = grid_for((const void *)init_random_kernel, kBlock, 0);
+    init_random_kernel<<<grid, kBlock, 0, s>>>(st, hash_base(seed, kStreamInit, 0), err);
+    return cudaGetLastError();
+}
+
+// Lists from a given graph: validate (in range, != u, distinct), compute
+// distances, sort.  err |= 2 on an invalid row.
+__global__ void __launch_bounds__(kBlock) init_graph_kernel(DevState st, const int32_t *__restrict__ ids,
+                                                            const uint8_t *__restrict__ is_new, int *err) {
+    const unsigned lane = lane_id();
+    const int K = st.K;
+    const float4 *X4 = reinterpret_cast<const float4 *>(st.X);
+    for (long long u = gwarp(); u < st.n; u += nwarps()) {
+        bool valid = (int)lane < K;
+        int32_t v = valid ? ids[(size_t)u * K + lane] : -1 - (int)lane;
+        bool bad = valid && (v < 0 || v >= st.n || v == u);
+        unsigned same = __match_any_sync(kFull, v);
+        bad = bad || (valid && __popc(same) > 1);
+        if (__any_sync(kFull, bad)) {
+            if (lane == 0) atomicOr(err, 2);
+            v = valid ? (int32_t)((u + 1 + lane) % st.n) : 0;
+        }
+        uint64_t key = kKeyEmpty;
+        if (valid) {
+            float dd = l2sq_rows(X4 + (size_t)u * st.nv, X4 + (size_t)v * st.nv, st.nv);
+            key = make_key(dd, (uint32_t)v, is_new[(size_t)u * K + lane] ? kFlagNew : 0u);
+        }
+        key = warp_sort_u64(key);
+        if (valid) st.keys[(size_t)u * K + lane] = key;
+    }
+}
+
+cudaError_t launch_init_graph(const DevState &st, const int32_t *ids, const uint8_t *is_new, int *err,
+                              cudaStream_t s) {
+    int grid = grid_for((const void *)init_graph_kernel, kBlock, 0);
+    init_graph_kernel<<<grid, kBlock, 0, s>>>(st, ids, is_new, err);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- degree count ----
+// Section 3.1 keeps |N(u)| known during the pass; here the reverse degrees
+// are counted per flag in one edge pass before sampling (forward degrees are
+// counted by the sampling warp itself).
+__global__ void count_kernel(DevState st, int li) {
+    if (iteration_skipped(st, li)) return;
+    const int64_t total = st.n * (int64_t)st.K;
+    // the reverse candidate fill counters of the previous iteration are no
+    // longer needed: restart them for this iteration's sampling
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < st.n; u += (int64_t)gridDim.x * blockDim.x) {
+        st.fill_new[u] = 0;
+        st.fill_old[u] = 0;
+    }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t key = st.keys[e];
+        uint32_t v = key_id(key);
+        atomicAdd((key & kFlagNew) ? &st.rev_new[v] : &st.rev_old[v], 1);
+    }
+}
+
+cudaError_t launch_count(const DevState &st, int li, cudaStream_t s) {
+    int grid = grid_for((const void *)count_kernel, 256, 0);
+    count_kernel<<<grid, 256, 0, s>>>(st, li);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- sampling ----
+// Section 3.1, one pass over the edges: edge (u, v) with flag f enters u's
+// forward candidates of kind f with probability min(1, s / fwd_f(u)) and u
+// enters v's reverse candidates of kind f with probability
+// min(1, s / rev_f(v)), from two independent hash streams keyed by (u, j).
+// Accepted forward new entries lose their "new" flag; every entry loses the
+// "inserted this iteration" flag.  Forward candidates are written compacted
+// by u's warp; reverse ones take an atomic slot in v's reverse part (capacity
+// R, overflow counted).
+__global__ void __launch_bounds__(kBlock) sample_kernel(DevState st, int li, uint64_t fbase, uint64_t rbase) {
+    if (iteration_skipped(st, li)) return;
+    const unsigned lane = lane_id();
+    const int K = st.K;
+    const uint32_t s = (uint32_t)st.s;
+    long long overflow = 0;
+    for (long long u = gwarp(); u < st.n; u += nwarps()) {
+        const bool valid = (int)lane < K;
+        uint64_t key = valid ? st.keys[(size_t)u * K + lane] : kKeyEmpty;
+        const bool isnew = valid && (key & kFlagNew);
+        const unsigned nm = __ballot_sync(kFull, isnew);
+        const uint32_t cnew = __popc(nm), cold = (uint32_t)K - cnew;
+        const uint32_t v = key_id(key);
+        bool accf = false;
+        if (valid) accf = accept(hash_uj(fbase, (uint64_t)u, lane), isnew ? cnew : cold, s);
+        const unsigned mn = __ballot_sync(kFull, accf && isnew);
+        const unsigned mo = __ballot_sync(kFull, accf && !isnew);
+        if (accf && isnew) st.cand_new[(size_t)u * st.cap + __popc(mn & lanemask_lt())] = (int)v;
+        if (accf && !isnew) st.cand_old[(size_t)u * st.cap + __popc(mo & lanemask_lt())] = (int)v;
+        if (lane == 0) {
+            st.fwd_new[u] = __popc(mn);
+            st.fwd_old[u] = __popc(mo);
+        }
+        if (valid) {
+            const int rc = isnew ? st.rev_new[v] : st.rev_old[v];
+            if (accept(hash_uj(rbase, (uint64_t)u, lane), (uint32_t)rc, s)) {
+                int slot = atomicAdd(isnew ? &st.fill_new[v] : &st.fill_old[v], 1);
+                if (slot < st.R)
+                    (isnew ? st.cand_new : st.cand_old)[(size_t)v * st.cap + K + slot] = (int)u;
+                else
+                    ++overflow;
+            }
+            uint64_t nk = key & ~(uint64_t)kFlagIns;
+            if (accf && isnew) nk &= ~(uint64_t)kFlagNew;
+            if (nk != key) st.keys[(size_t)u * K + lane] = nk;
+        }
+    }
+    overflow = warp_sum(overflow);
+    if (lane == 0 && overflow) atomic_add_ll(&st.stats[kStatRevOverflow], overflow);
+}
+
+cudaError_t launch_sample(const DevState &st, int li, int it, uint64_t seed, cudaStream_t s) {
+    int grid = grid_for((const void *)sample_kernel, kBlock, 0);
+    sample_kernel<<<grid, kBlock, 0, s>>>(st, li, hash_base(seed, kStreamFwd, (uint32_t)it),
+                                          hash_base(seed, kStreamRev, (uint32_t)it));
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------- greedy relabelling ----
+// Section 3.2, Algorithm 1, exact and sequential: spot i = 0 .. n-2 looks at
+// the list a_i of the node on spot i (reading_b: node i), ascending; the first
+// entry x not yet placed before spot i+1 either already holds spot i+1 (stop)
+// or is moved there, the previous holder y of spot i+1 taking x's old spot p
+// (the value of sigma(x) before the first swap).  One warp runs the whole
+// chain: lanes hold the K list entries and test their spots in parallel; the
+// first qualifying lane is found with a ballot.
+__global__ void __launch_bounds__(32) greedy_reorder_kernel(const uint64_t *__restrict__ keys, int64_t n, int K,
+                                                            int reading_b, int32_t *sigma, int32_t *sigma_inv) {
+    const unsigned lane = lane_id();
+    for (int64_t i = lane; i < n; i += 32) {
+        sigma[i] = (int32_t)i;
+        sigma_inv[i] = (int32_t)i;
+    }
+    __syncwarp();
+    int32_t node = 0;  // node on spot i (reading A); kept in a register across steps
+    for (int64_t i = 0; i + 1 < n; ++i) {
+        const int64_t who = reading_b ? i : node;
+        int32_t x = -1;
+        int64_t p = -1;
+        if ((int)lane < K) {
+            x = (int32_t)key_id(__ldg(keys + (size_t)who * K + lane));
+            p = ((volatile int32_t *)sigma)[x];
+        }
+        const unsigned later = __ballot_sync(kFull, (int)lane < K && p >= i + 1);
+        int32_t next_node;
+        const int32_t held = ((volatile int32_t *)sigma_inv)[i + 1];
+        if (later == 0) {
+            next_node = held;
+        } else {
+            const int src = __ffs(later) - 1;
+            const int32_t xs = __shfl_sync(kFull, x, src);
+            const int64_t ps = __shfl_sync(kFull, p, src);
+            if (ps == i + 1) {
+                next_node = xs;
+            } else {
+                if (lane == 0) {
+                    sigma[xs] = (int32_t)(i + 1);
+                    sigma[held] = (int32_t)ps;
+                    sigma_inv[i + 1] = xs;
+                    sigma_inv[ps] = held;
+                }
+                next_node = xs;
+            }
+        }
+        __syncwarp();
+        node = next_node;
+    }
+}
+
+cudaError_t launch_greedy_reorder(const uint64_t *keys, int64_t n, int K, int reading_b, int32_t *sigma,
+                                  int32_t *sigma_inv, cudaStream_t s) {
+    greedy_reorder_kernel<<<1, 32, 0, s>>>(keys, n, K, reading_b, sigma, sigma_inv);
+    return cudaGetLastError();
+}
+
+// Move node u to spot sigma(u) (Section 3.2, all at once): its padded row and
+// its list, ids renamed through sigma and re-sorted by (dist, new id).  The
+// total relabelling original -> spot is composed with sigma.
+__global__ void __launch_bounds__(kBlock) permute_kernel(DevState st, float *__restrict__ X_dst,
+                                                         uint64_t *__restrict__ keys_dst,
+                                                         const int32_t *__restrict__ sigma,
+                                                         int32_t *__restrict__ total_perm) {
+    const unsigned lane = lane_id();
+    const int K = st.K;
+    const float4 *X4 = reinterpret_cast<const float4 *>(st.X);
+    float4 *D4 = reinterpret_cast<float4 *>(X_dst);
+    for (long long u = gwarp(); u < st.n; u += nwarps()) {
+        const int32_t p = sigma[u];
+        for (int c = lane; c < st.nv; c += 32) D4[(size_t)p * st.nv + c] = X4[(size_t)u * st.nv + c];
+        uint64_t key = kKeyEmpty;
+        if ((int)lane < K) {
+            uint64_t k0 = st.keys[(size_t)u * K + lane];
+            key = (k0 & 0xFFFFFFFF00000003ull) | ((uint64_t)(uint32_t)sigma[key_id(k0)] << 2);
+        }
+        key = warp_sort_u64(key);
+        if ((int)lane < K) keys_dst[(size_t)p * K + lane] = key;
+        if (lane == 0) total_perm[u] = sigma[total_perm[u]];
+    }
+}
+
+cudaError_t launch_permute(const DevState &src, float *X_dst, uint64_t *keys_dst, const int32_t *sigma,
+                           int32_t *total_perm, cudaStream_t s) {
+    int grid = grid_for((const void *)permute_kernel, kBlock, 0);
+    permute_kernel<<<grid, kBlock, 0, s>>>(src, X_dst, keys_dst, sigma, total_perm);
+    return cudaGetLastError();
+}
+
+__global__ void iota_kernel(int32_t *__restrict__ p, int64_t n) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        p[u] = (int32_t)u;
+}
+
+cudaError_t launch_iota(int32_t *p, int64_t n, cudaStream_t s) {
+    int grid = grid_for((const void *)iota_kernel, 256, 0);
+    iota_kernel<<<grid, 256, 0, s>>>(p, n);
+    return cudaGetLastError();
+}
+
+__global__ void invert_kernel(const int32_t *__restrict__ perm, int64_t n, int32_t *__restrict__ inv) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        inv[perm[u]] = (int32_t)u;
+}
+
+cudaError_t launch_invert(const int32_t *perm, int64_t n, int32_t *inv, cudaStream_t s) {
+    int grid = grid_for((const void *)invert_kernel, 256, 0);
+    invert_kernel<<<grid, 256, 0, s>>>(perm, n, inv);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ re-rank + output ----
+// Final lists in the caller's labelling: original node u's list lives at spot
+// total_perm[u]; every entry's distance is recomputed with the canonical
+// float32 difference form, ids are renamed back, and the row is re-sorted by
+// (dist, original id).
+__global__ void __launch_bounds__(kBlock) output_kernel(DevState st, const int32_t *__restrict__ total_perm,
+                                                        const int32_t *__restrict__ total_inv,
+                                                        int32_t *__restrict__ ids, float *__restrict__ dists) {
+    const unsigned lane = lane_id();
+    const int K = st.K;
+    const float4 *X4 = reinterpret_cast<const float4 *>(st.X);
+    for (long long u = gwarp(); u < st.n; u += nwarps()) {
+        const int64_t p = total_perm ? total_perm[u] : u;
+        uint64_t key = kKeyEmpty;
+        if ((int)lane < K) {
+            uint32_t v = key_id(st.keys[(size_t)p * K + lane]);
+            float dd = l2sq_rows(X4 + (size_t)p * st.nv, X4 + (size_t)v * st.nv, st.nv);
+            uint32_t vo = total_inv ? (uint32_t)total_inv[v] : v;
+            key = make_key(dd, vo, 0);
+        }
+        key = warp_sort_u64(key);
+        if ((int)lane < K) {
+            ids[(size_t)u * K + lane] = (int32_t)key_id(key);
+            dists[(size_t)u * K + lane] = key_dist(key);
+        }
+    }
+}
+
+cudaError_t launch_output(const DevState &st, const int32_t *total_perm, const int32_t *total_inv,
+                          int32_t *ids, float *dists, cudaStream_t s) {
+    int grid = grid_for((const void *)output_kernel, kBlock, 0);
+    output_kernel<<<grid, kBlock, 0, s>>>(st, total_perm, total_inv, ids, dists);
+    return cudaGetLastError();
+}
+
+}  // namespace knng

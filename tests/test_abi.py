@@ -1,0 +1,81 @@
+"""The C ABI library loads and exports every entry point include/knng.h
+declares; argument checks that return before any CUDA call.  CPU only."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "knng.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2112_06630_gb300 import build as b
+    b.build()
+    import paper_2112_06630_gb300 as knng
+    return knng.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(knng_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_calls():
+    names = declared_functions()
+    for must in ("knng_build", "knng_init", "knng_iterate", "knng_get", "knng_destroy", "knng_bruteforce",
+                 "knng_reorder", "knng_strerror"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [f for f in declared_functions() if not hasattr(lib, f)]
+    assert missing == []
+
+
+def test_signatures_are_plain_c():
+    src = open(HEADER).read()
+    assert "torch" not in src and "at::" not in src and "std::" not in src
+    assert 'extern "C"' in src
+
+
+def test_strerror_and_version(lib):
+    import paper_2112_06630_gb300 as knng
+    assert knng.strerror(0) == "ok"
+    assert "invalid" in knng.strerror(-1)
+    assert "sm_103a" in knng.version()
+
+
+@pytest.mark.parametrize("n,d,K,rho,delta", [
+    (1, 4, 1, 0.5, 0.0),      # n < 2
+    (10, 0, 3, 0.5, 0.0),     # d < 1
+    (10, 4, 0, 0.5, 0.0),     # K < 1
+    (10, 4, 10, 0.5, 0.0),    # K > n-1
+    (10, 4, 3, 0.0, 0.0),     # rho <= 0
+    (10, 4, 3, 1.5, 0.0),     # rho > 1
+    (10, 4, 3, 0.5, -1.0),    # delta < 0
+])
+def test_invalid_arguments_rejected_before_any_device_work(lib, n, d, K, rho, delta):
+    x = np.zeros((max(n, 1), max(d, 1)), np.float32)
+    ids = np.zeros((max(n, 1), max(K, 1)), np.int32)
+    dists = np.zeros((max(n, 1), max(K, 1)), np.float32)
+    rc = lib.knng_build(x.ctypes.data, n, d, K, rho, delta, 5, 0, ids.ctypes.data, dists.ctypes.data)
+    assert rc == -1
+
+
+def test_k_above_32_unsupported(lib):
+    x = np.zeros((100, 4), np.float32)
+    ids = np.zeros((100, 40), np.int32)
+    dists = np.zeros((100, 40), np.float32)
+    assert lib.knng_build(x.ctypes.data, 100, 4, 40, 0.5, 0.0, 5, 0, ids.ctypes.data, dists.ctypes.data) == -5
+
+
+def test_null_pointers_rejected(lib):
+    h = ctypes.c_void_p()
+    assert lib.knng_init(ctypes.byref(h), None, 10, 4, 3, 0.5, 0.0, 0, 0, None) == -1
+    assert lib.knng_iterate(None, None) == -1
+    assert lib.knng_destroy(None) == 0

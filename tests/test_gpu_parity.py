@@ -1,0 +1,252 @@
+"""GPU parity: every CUDA step against the CPU oracle on the same seeded
+inputs, through the C ABI.
+
+Integer-valued inputs make every squared distance an exact float32 integer on
+both sides, so there the two implementations must agree bit for bit (ids,
+distances, flags, change counts), including ties, which both break by id.
+Real-valued inputs are compared with the tolerances of the method: ids equal
+up to ties (|d_a - d_b| <= 1e-5 d_b), distances within 1e-5 relative (brute
+force), recall within 0.005 of the oracle's, every returned distance within
+1e-4 relative of its float64 recomputation.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import metrics
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2112_06630_gb300 as knng  # noqa: E402
+
+
+def _int_data(n, d, hi, seed, density=1.0):
+    g = np.random.default_rng(seed)
+    x = g.integers(0, hi, size=(n, d))
+    if density < 1.0:
+        x = np.where(g.random((n, d)) < density, x, 0)
+    return x.astype(np.float32)
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def assert_ids_up_to_ties(gi, gd, oi, od, rtol=1e-5):
+    gi, gd = np.asarray(gi), np.asarray(gd)
+    np.testing.assert_allclose(gd, od, rtol=rtol, atol=1e-7)
+    mism = gi != oi
+    if mism.any():
+        assert np.allclose(gd[mism], od[mism], rtol=rtol, atol=1e-7)
+
+
+# ------------------------------------------------------------ brute force ----
+
+@pytest.mark.parametrize("n,d,K", [(2000, 8, 10), (1037, 5, 7), (700, 33, 16), (513, 16, 32), (300, 130, 20),
+                                   (2, 3, 1), (33, 4, 32)])
+def test_bruteforce_matches_oracle(n, d, K):
+    x = workloads.uniform(n, d, seed=n + d)
+    gi, gd = knng.knng_bruteforce(_cuda(x), K)
+    oi, od = oracle.bruteforce(x, K)
+    assert_ids_up_to_ties(gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+
+
+def test_bruteforce_integer_data_bit_exact_with_ties():
+    x = _int_data(1500, 12, 4, seed=1)     # many equal distances
+    gi, gd = knng.knng_bruteforce(_cuda(x), 20)
+    oi, od = oracle.bruteforce(x, 20)
+    assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+def test_bruteforce_query_rows_and_host_pointers():
+    x = workloads.gaussian_mixture(5000, 16, 20, seed=3)
+    rows = np.array([0, 4999, 17, 2500, 1234], np.int64)
+    gi, gd = knng.knng_bruteforce(x, 20, rows=rows)          # host in, host out
+    oi, od = oracle.bruteforce(x, 20, rows)
+    assert_ids_up_to_ties(gi, gd, oi, od)
+
+
+def test_bruteforce_duplicate_points():
+    x = np.zeros((300, 8), np.float32)
+    x[150:] = 1.0
+    gi, gd = knng.knng_bruteforce(_cuda(x), 5)
+    oi, od = oracle.bruteforce(x, 5)
+    assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+# ------------------------------------------------------------ random init ----
+
+@pytest.mark.parametrize("n,d,K", [(3001, 8, 10), (500, 3, 20), (33, 5, 32), (2, 1, 1)])
+def test_init_matches_oracle_exactly(n, d, K):
+    x = _int_data(n, d, 16, seed=K)
+    with knng.Context(_cuda(x), K, rho=0.5, seed=7) as c:
+        gi, gd, gf = c.state()
+    st = oracle.State(x, K, 0.5, seed=7)
+    st.init_random()
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+
+
+# ------------------------------------------------------ sampling + join ----
+
+CASES = [
+    # n, d, K, rho, int range  (spans several warps/blocks, ragged tails,
+    # each list-size template, padded and unpadded rows, the global-row path)
+    (3001, 8, 10, 1.0, 16),
+    (2500, 16, 20, 0.5, 8),
+    (1800, 3, 16, 0.5, 6),
+    (1200, 17, 32, 0.3, 5),
+    (900, 40, 8, 0.5, 4),
+    (400, 600, 12, 0.5, 3),
+]
+
+
+@pytest.mark.parametrize("n,d,K,rho,hi", CASES)
+def test_one_iteration_matches_oracle_bit_exact(n, d, K, rho, hi):
+    x = _int_data(n, d, hi, seed=n)
+    ids0, new0 = workloads.random_graph(n, K, seed=n + 1, p_new=0.6)
+    with knng.Context(_cuda(x), K, rho=rho, seed=11, graph=(ids0, new0), iter=0) as c:
+        conv, ch = c.iterate()
+        gnew, gold = c.samples()
+        gi, gd, gf = c.state()
+        stats = c.stats()
+    st = oracle.State(x, K, rho, seed=11)
+    st.init_graph(ids0, new0, 0)
+    r = st.iterate()
+    assert stats["rev_overflow"] == 0 and stats["set_overflow"] == 0
+    onew, oold = st.samples()
+    for u in range(n):
+        sn = set(gnew[u].tolist())
+        assert sn == set(onew[u].tolist())
+        assert set(gold[u].tolist()) - sn == set(oold[u].tolist())
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    assert ch == r["changes"]
+    assert stats["dist_evals"] == r["evals"]
+
+
+def test_several_iterations_match_oracle_bit_exact():
+    n, d, K, rho = 4000, 8, 12, 0.5
+    x = _int_data(n, d, 10, seed=5)
+    st = oracle.State(x, K, rho, seed=3)
+    st.init_random()
+    with knng.Context(_cuda(x), K, rho=rho, seed=3) as c:
+        for it in range(6):
+            conv, ch = c.iterate()
+            r = st.iterate()
+            gi, gd, gf = c.state()
+            oi, od, of = st.state()
+            assert (gi == oi).all() and (gd == od).all() and (gf == of).all(), f"iteration {it + 1}"
+            assert ch == r["changes"]
+
+
+# ------------------------------------------------------------ Algorithm 1 ----
+
+def test_alg1_golden_on_gpu():
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "alg1_line5.json")))
+    x = np.array(g["points_1d"], np.float32)[:, None]
+    lists = np.array(g["lists"], np.int32)
+    for rd, flag in (("a", knng.FLAG_REORDER), ("b", knng.FLAG_REORDER | knng.FLAG_REORDER_B)):
+        with knng.Context(_cuda(x), g["K"], rho=1.0, flags=flag,
+                          graph=(lists, np.ones_like(lists, np.uint8))) as c:
+            c.reorder()
+            assert c.permutation().tolist() == g[f"sigma_reading_{rd}"]
+
+
+@pytest.mark.parametrize("reading_b", [False, True])
+def test_alg1_matches_oracle(reading_b):
+    n, K = 6000, 10
+    x = _int_data(n, 6, 20, seed=9)
+    ei, _ = oracle.bruteforce(x, K)
+    flags = knng.FLAG_REORDER | (knng.FLAG_REORDER_B if reading_b else 0)
+    with knng.Context(_cuda(x), K, rho=1.0, flags=flags, graph=(ei, np.ones_like(ei, np.uint8))) as c:
+        c.reorder()
+        sg = c.permutation()
+        gi, gd, _ = c.state()
+    osg, osi = oracle.greedy_reorder(ei, reading_b)
+    assert (sg == osg).all()
+    # lists were moved to their new spots with renamed ids
+    ri = osg[ei]
+    for u in range(0, n, 97):
+        assert set(gi[osg[u]].tolist()) == set(ri[u].tolist())
+
+
+def test_build_with_reorder_matches_oracle_bit_exact():
+    n, d, K = 3000, 8, 10
+    x = _int_data(n, d, 12, seed=21)
+    gi, gd, st = knng.knng_build(_cuda(x), K, rho=0.5, delta=0.002, max_iters=8, seed=4, flags=knng.FLAG_REORDER)
+    oi, od, ost = oracle.build_knng(x, K, 0.5, 0.002, 8, seed=4, reorder=1)
+    assert st["reordered"] == 1 and ost["reordered"]
+    assert st["iterations"] == ost["iters"]
+    assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+def test_build_plain_matches_oracle_bit_exact():
+    n, d, K = 5000, 6, 16
+    x = _int_data(n, d, 9, seed=2)
+    gi, gd, st = knng.knng_build(_cuda(x), K, rho=0.5, delta=0.001, max_iters=12, seed=9)
+    oi, od, ost = oracle.build_knng(x, K, 0.5, 0.001, 12, seed=9)
+    assert st["iterations"] == ost["iters"] and st["dist_evals"] == ost["evals"]
+    assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+# ------------------------------------------------------- whole builds ----
+
+def test_uniform_n2k_recall_and_invariants():
+    """2,000 uniform points in [0,1)^8, K=10, rho=1, delta=0.001, 10 iterations."""
+    w, x = workloads.make("uniform_n2k_d8")
+    ei, _ = oracle.bruteforce(x, w.K)
+    gi, gd, st = knng.knng_build(_cuda(x), w.K, w.rho, w.delta, w.max_iters, seed=0)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    assert metrics.check_graph(x, gi, gd) == []
+    oi, od, ost = oracle.build_knng(x, w.K, w.rho, w.delta, w.max_iters, seed=0, count_mode="inplace")
+    rg, ro = metrics.recall(x, gi, ei), metrics.recall(x, oi, ei)
+    assert rg >= 0.99
+    assert abs(rg - ro) <= 0.005
+
+
+def test_host_and_device_pointers_agree():
+    x = workloads.gaussian_mixture(3000, 16, 10, seed=1)
+    hi, hd, _ = knng.knng_build(x, 10, 0.5, 0.001, 8, seed=2)             # host in/out
+    di, dd, _ = knng.knng_build(_cuda(x), 10, 0.5, 0.001, 8, seed=2)      # device in/out
+    assert (hi == di.cpu().numpy()).all() and (hd == dd.cpu().numpy()).all()
+
+
+def test_complete_graph_k_equals_n_minus_1():
+    x = workloads.uniform(33, 4, seed=3)
+    gi, gd, st = knng.knng_build(_cuda(x), 32, 1.0, 0.0, 2, seed=0)
+    oi, od = oracle.bruteforce(x, 32)
+    assert_ids_up_to_ties(gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+
+
+def test_all_points_equal():
+    x = np.ones((500, 8), np.float32)
+    gi, gd, st = knng.knng_build(_cuda(x), 10, 0.5, 0.0, 3, seed=0)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    assert (gd == 0).all()
+    assert metrics.check_graph(x, gi, gd) == []
+
+
+def test_clustered_n100k_full_size_sampled_parity():
+    """The benchmark's workload and launch configuration: 100,000 points, 16
+    dims, 50 clusters, K=20, rho=0.5, delta=0.001, 15 iterations.  Recall on
+    2,000 sampled rows (oracle brute force, one row at a time) must be >= the
+    oracle's recall - 0.005; sampled distances within 1e-4 of float64."""
+    w, x = workloads.make("clustered_n100k_d16")
+    rows = np.random.default_rng(0).choice(w.n, 2000, replace=False)
+    ei, _ = oracle.bruteforce(x, w.K, rows)
+    gi, gd, st = knng.knng_build(_cuda(x), w.K, w.rho, w.delta, w.max_iters, seed=0)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    assert metrics.check_graph(x, gi, gd, rows=rows) == []
+    oi, od, ost = oracle.build_knng(x, w.K, w.rho, w.delta, w.max_iters, seed=0, count_mode="inplace")
+    rg = metrics.recall(x, gi, ei, rows)
+    ro = metrics.recall(x, oi, ei, rows)
+    assert rg >= ro - 0.005, (rg, ro)
+    assert st["lock_timeouts"] == 0
