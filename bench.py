@@ -1,0 +1,307 @@
+"""Benchmark: K-NNG build time by NN-Descent on one GB300 (and N replicas).
+
+Workload: 100,000 points in 16 dimensions from an equal-weight mixture of 50
+Gaussian clusters (centres uniform in [-10, 10]^16, sigma 1), K = 20,
+rho = 0.5, delta = 0.001, at most 15 iterations, seed 0; float32 throughout.
+
+A step is one whole build (random init, every iteration that runs, re-ranked
+output) with the points already resident on the device.  The L2 cache is
+flushed (a 256 MiB device write) between timed steps, outside the timed
+region.  With --gpus N (torchrun) every rank builds its own replica: the path
+has no exchange step, so the ranks share nothing but the barrier and the
+max-over-ranks of the step time.
+
+Printed (rank 0, one JSON line): the build time, recall@K on 2,000 sampled
+rows against the GPU brute force, distance evaluations per second, the
+end-to-end time through the public API with host buffers, the roofline of the
+local-join kernel, and the CPU oracle timed on this host.
+
+--impl reference times the CPU oracle (plain C, one thread) on the same
+workload instead: the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+WORKLOAD = "clustered_n100k_d16"
+METRIC = "K-NNG build s at recall@K>=0.99"
+RECALL_ROWS = 2000
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([c.strip() for c in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) > 8:
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _max_over_ranks(v: float, ws: int, device):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def join_bytes(st: dict, dp: int) -> float:
+    """Algorithmic bytes moved by the local-join launches of one build: every
+    candidate id read (4 B), every gathered candidate row (dp * 4 B) with its
+    worst-key snapshot (8 B), and for every locked merge one K-key list read
+    and written (2 * K * 8 B)."""
+    return (st["cand_ids"] * 4.0 + st["gathered_rows"] * (dp * 4.0 + 8.0)
+            + st["merges"] * 2.0 * st["K"] * 8.0)
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_2112_06630_gb300 as knng
+    from oracle import metrics
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    w, x = workloads.make(WORKLOAD)
+    xd = torch.from_numpy(x).to(device)
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    flags = knng.FLAG_REORDER if args.reorder else 0
+    dp = (w.d + 3) // 4 * 4
+
+    def build(tflags=0):
+        return knng.knng_build(xd, w.K, w.rho, w.delta, w.max_iters, seed=0, flags=flags | tflags)
+
+    for _ in range(args.warmup):
+        build()
+    torch.cuda.synchronize()
+
+    times, stats = [], None
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            _barrier(ws)
+            torch.cuda.synchronize()
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            ids, dists, stats = build()
+            e.record(stream)
+            torch.cuda.synchronize()
+            _barrier(ws)
+            times.append(s.elapsed_time(e) / 1e3)
+    step_s = _max_over_ranks(sum(times) / len(times), ws, device)
+    clocks = clk.summary()
+
+    # the local-join kernel: per-launch time from CUDA events recorded by the
+    # library on the launching stream, algorithmic bytes from device counters
+    flush.fill_(1)
+    torch.cuda.synchronize()
+    _, _, tst = build(knng.FLAG_TIMING)
+    torch.cuda.synchronize()
+
+    # end to end through the public API: pinned host input, host outputs
+    xh = torch.from_numpy(x).pin_memory()
+    oi = torch.empty((w.n, w.K), dtype=torch.int32).pin_memory()
+    od = torch.empty((w.n, w.K), dtype=torch.float32).pin_memory()
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        knng.knng_build(xh, w.K, w.rho, w.delta, w.max_iters, seed=0, flags=flags, out=(oi, od))
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e.append(t1 - t0)
+    e2e_s = _max_over_ranks(sum(e2e) / len(e2e), ws, device)
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    rows = np.random.default_rng(0).choice(w.n, RECALL_ROWS, replace=False)
+    bi, _ = knng.knng_bruteforce(xd, w.K, rows=torch.from_numpy(rows).to(device))
+    rec = metrics.recall(x, ids.cpu().numpy(), bi.cpu().numpy(), rows)
+
+    peaks = _peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    ran = max(1, tst["join_ran"])
+    jb = join_bytes(tst, dp) / ran
+    jt = tst["join_ms_ran"] / 1e3 / ran
+    achieved = jb / jt / 1e9
+    roof = {"kernel": "join_kernel", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+            "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+            "peak_source": "measured" if peaks else "fallback",
+            "bytes_per_launch": round(jb), "launch_ms": round(jt * 1e3, 4), "launches": ran}
+
+    cpu = None
+    if not args.no_cpu and ws == 1:
+        cpu = cpu_baseline(w, x)
+
+    n_builds = ws
+    value = step_s / n_builds
+    line = {
+        "metric": METRIC, "value": round(value, 6), "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
+                   "max_iters": w.max_iters, "reorder": bool(args.reorder), "parallelism": f"replicas{ws}",
+                   "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
+        "recall_at_k": round(rec, 5), "recall_rows": RECALL_ROWS,
+        "iterations": stats["iterations"], "dist_evals": stats["dist_evals"],
+        "dist_evals_per_s": round(stats["dist_evals"] / (step_s), 1),
+        "paper_flops_per_s": round(stats["dist_evals"] * (3 * w.d - 1) / step_s, 1),
+        "e2e": {"value": round(e2e_s / n_builds, 6), "unit": "s", "h2d_bytes_per_step": int(x.nbytes),
+                "d2h_bytes_per_step": int(w.n * w.K * 8)},
+        "gpu_launches": int(stats["kernel_launches"]) * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, x, builds: int = 1):
+    """The oracle as it stands (plain C, one thread, in-place count mode) on
+    the full workload; seconds per build."""
+    import oracle
+    ts = []
+    for _ in range(builds):
+        t0 = time.perf_counter()
+        oracle.build_knng(x, w.K, w.rho, w.delta, w.max_iters, seed=0, count_mode="inplace")
+        ts.append(time.perf_counter() - t0)
+    return {"value": round(sum(ts) / len(ts), 4), "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"whole workload ({w.n} points), {builds} build(s), single thread"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    w, x = workloads.make(WORKLOAD)
+    import oracle
+    oracle._load()
+    for _ in range(args.warmup):
+        cpu_baseline(w, x)
+    ts = [cpu_baseline(w, x)["value"] for _ in range(args.steps)]
+    v = sum(ts) / len(ts)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 2),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
+                   "max_iters": w.max_iters, "parallelism": "cpu1"},
+        "cpu_baseline": {"value": round(v, 4), "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": f"whole workload ({w.n} points) per step, single thread"},
+        "e2e": {"value": round(v, 4), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--reorder", action="store_true", help="Algorithm 1 relabelling after iteration 1")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        print("note: at least 3 warm-up steps are required; using 3", file=sys.stderr)
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

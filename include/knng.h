@@ -76,9 +76,13 @@ typedef struct knng_stats {
     int64_t set_overflow;      /* candidates skipped beyond 64 per node and iteration */
     int64_t lock_timeouts;     /* bounded lock waits that gave up (then KNNG_ERR_TIMEOUT) */
     int64_t kernel_launches;   /* kernels this context launched */
+    int64_t cand_ids;          /* sampled candidate ids read by the local join */
     int32_t reordered;         /* 1 once Algorithm 1 relabelled the points */
     int32_t join_launches;     /* local-join launches timed (KNNG_FLAG_TIMING) */
     double join_ms;            /* their summed CUDA-event time */
+    int32_t join_ran;          /* timed launches whose iteration ran (not skipped) */
+    int32_t reserved;
+    double join_ms_ran;        /* summed time of those launches */
 } knng_stats;
 
 /*

@@ -78,7 +78,7 @@ struct knng_ctx {
     long long *stats = nullptr, *it_stats = nullptr;
 
     std::vector<cudaEvent_t> ev;  // start/stop pairs around join launches
-    int timed = 0;
+    std::vector<int> ev_li;       // iteration index of each pair
 
     DevState dev(bool gate) const {
         DevState st;
@@ -256,6 +256,7 @@ int enqueue_iteration(knng_ctx *c, bool gate) {
         KNNG_TRY(cudaEventCreate(&b));
         c->ev.push_back(a);
         c->ev.push_back(b);
+        c->ev_li.push_back(li);
         KNNG_TRY(cudaEventRecord(a, c->stream));
     }
     KNNG_TRY(launch_join(st, li, c->stream));
@@ -489,12 +490,19 @@ int knng_get_stats(knng_ctx *c, knng_stats *out) {
     out->lock_timeouts = st[kStatLockTimeout];
     out->kernel_launches = c->launches;
     out->reordered = c->reordered ? 1 : 0;
+    out->cand_ids = 0;
+    for (int i = 0; i < c->li; ++i) out->cand_ids += its[(size_t)i * kItCount + kItCandIds];
     out->join_ms = 0;
+    out->join_ms_ran = 0;
     for (size_t i = 0; i + 1 < c->ev.size(); i += 2) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) {
             out->join_ms += ms;
             out->join_launches++;
+            if (its[(size_t)c->ev_li[i / 2] * kItCount + kItRan]) {
+                out->join_ms_ran += ms;
+                out->join_ran++;
+            }
         } else {
             cudaGetLastError();
         }

@@ -241,9 +241,15 @@ cudaError_t launch_join_t(const DevState &st, int li, cudaStream_t s) {
     const JoinLayout lay = join_layout(st.cap, st.nv, S);
     const size_t dyn = lay.per_warp * kJoinWarps;
     auto kern = join_kernel<KMAX, S>;
-    if (dyn > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    static bool opted_in = false;  // allow up to the per-block maximum once
+    if (!opted_in) {
+        int dev = 0, mx = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             mx - 1024);
         if (e != cudaSuccess) return e;
+        opted_in = true;
     }
     const int grid = grid_for((const void *)kern, kJoinWarps * 32, dyn);
     kern<<<grid, kJoinWarps * 32, dyn, s>>>(st, li);
@@ -253,7 +259,7 @@ cudaError_t launch_join_t(const DevState &st, int li, cudaStream_t s) {
 template <int KMAX>
 cudaError_t launch_join_k(const DevState &st, int li, cudaStream_t s) {
     const JoinLayout lay = join_layout(st.cap, st.nv, true);
-    if (lay.per_warp * kJoinWarps <= 160 * 1024) return launch_join_t<KMAX, true>(st, li, s);
+    if (lay.per_warp * kJoinWarps <= 110 * 1024) return launch_join_t<KMAX, true>(st, li, s);
     return launch_join_t<KMAX, false>(st, li, s);
 }
 }  // namespace
