@@ -185,6 +185,33 @@ int knng_destroy(knng_ctx *ctx);
 int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *rows,
                     int64_t nq, int32_t *ids, float *dists, void *stream);
 
+/*
+ * Brute-force K-NNG that allocates nothing, for callers that cannot allocate
+ * device memory: code that runs while a stream is being captured into a CUDA
+ * graph in global capture mode (where cudaMalloc is refused), programs whose
+ * device memory is owned entirely by their own pool allocator, and real-time
+ * callers that must not allocate after start-up.  The paper has no
+ * counterpart; it is the same computation as knng_bruteforce.
+ *
+ * data, ids, dists (and rows, when not NULL) must be device pointers of the
+ * current device, with the layouts of knng_bruteforce; the caller owns them.
+ * The only scratch, the zero-padded copy of the points, is a static device
+ * array of KNNG_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ * holds until the process exits.  Returns KNNG_ERR_INVALID_ARG when
+ * n * round_up(d, 4) * 4 exceeds KNNG_NOALLOC_SCRATCH_BYTES, or when a
+ * pointer is not a device pointer.
+ *
+ * The first call on a device looks up the array's device address (one
+ * cudaGetSymbolAddress, no allocation); make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last call's
+ * contents; each call overwrites the whole region it reads before reading it.
+ * Calls whose work overlaps on the GPU (other streams, other threads) race on
+ * the array: serialise them.  Enqueues on `stream`, does not synchronise.
+ */
+#define KNNG_NOALLOC_SCRATCH_BYTES (8u << 20)
+int knng_bruteforce_noalloc(const float *data, int64_t n, int d, int K, const int64_t *rows,
+                            int64_t nq, int32_t *ids, float *dists, void *stream);
+
 /* Name of a return code. */
 const char *knng_strerror(int code);
 

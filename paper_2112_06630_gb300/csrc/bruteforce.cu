@@ -7,6 +7,9 @@
 // candidate only when it beats the current K-th key.  Distances use the
 // library's canonical float32 difference form, so ground truth and NN-Descent
 // agree on the value of every pair.
+#include <mutex>
+
+#include "../../include/knng.h"
 #include "internal.h"
 
 namespace knng {
@@ -118,3 +121,68 @@ cudaError_t launch_bruteforce(const float *X, int64_t n, int dp, int K, const in
 }
 
 }  // namespace knng
+
+// ---------------------------------------------------------------------------
+// knng_bruteforce_noalloc: the brute-force K-NNG for callers that cannot
+// allocate device memory.  Its only scratch -- the zero-padded copy of the
+// points that the kernel reads -- lives in the file-scope device array below,
+// which is created with the module and stays resident on every GPU that loads
+// this library until the process exits.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) float knng_noalloc_points[KNNG_NOALLOC_SCRATCH_BYTES / sizeof(float)];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 256;
+float *g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device.  Looked up once
+// per device (host code cannot use the array's name as a device address).
+cudaError_t noalloc_scratch(float **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, knng_noalloc_points);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+bool noalloc_on_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" int knng_bruteforce_noalloc(const float *data, int64_t n, int d, int K, const int64_t *rows, int64_t nq,
+                                       int32_t *ids, float *dists, void *stream) {
+    if (!data || !ids || !dists || n < 2 || d < 1 || K < 1 || K > n - 1) return KNNG_ERR_INVALID_ARG;
+    if (K > knng::kMaxK) return KNNG_ERR_UNSUPPORTED;
+    const int dp = (d + 3) & ~3;
+    if ((uint64_t)n * (uint64_t)dp * sizeof(float) > (uint64_t)KNNG_NOALLOC_SCRATCH_BYTES)
+        return KNNG_ERR_INVALID_ARG;
+    if (!rows) nq = n;
+    if (nq < 1) return KNNG_ERR_INVALID_ARG;
+    if (!noalloc_on_device(data) || !noalloc_on_device(ids) || !noalloc_on_device(dists) ||
+        (rows && !noalloc_on_device(rows)))
+        return KNNG_ERR_INVALID_ARG;
+    float *X = nullptr;
+    cudaError_t e = noalloc_scratch(&X);
+    if (e != cudaSuccess) return KNNG_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // staging writes every element of the n x dp region it uses (padding
+    // included), so nothing left by an earlier call is read
+    e = knng::launch_stage(data, n, d, X, dp, s);
+    if (e == cudaSuccess) e = knng::launch_bruteforce(X, n, dp, K, rows, nq, ids, dists, s);
+    return e == cudaSuccess ? KNNG_OK : KNNG_ERR_CUDA;
+}
