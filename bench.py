@@ -122,12 +122,17 @@ def _barrier(ws):
 
 
 def join_bytes(st: dict, dp: int) -> float:
-    """Algorithmic bytes moved by the local-join launches of one build: every
+    """Algorithmic bytes of the local-join launches of one build: every
     candidate id read (4 B), every gathered candidate row (dp * 4 B) with its
-    worst-key snapshot (8 B), and for every locked merge one K-key list read
-    and written (2 * K * 8 B)."""
-    return (st["cand_ids"] * 4.0 + st["gathered_rows"] * (dp * 4.0 + 8.0)
-            + st["merges"] * 2.0 * st["K"] * 8.0)
+    worst-key snapshot (8 B), every proposal key written (8 B)."""
+    return st["cand_ids"] * 4.0 + st["gathered_rows"] * (dp * 4.0 + 8.0) + st["proposals"] * 8.0
+
+
+def merge_bytes(st: dict) -> float:
+    """Algorithmic bytes of the list-merge launches of one build: every
+    proposal key read (8 B), and per merged list one K-key list read and
+    written (2 * K * 8 B)."""
+    return st["proposals"] * 8.0 + st["merges"] * 2.0 * st["K"] * 8.0
 
 
 def run_gpu(args):
@@ -209,13 +214,17 @@ def run_gpu(args):
     peaks = _peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     ran = max(1, tst["join_ran"])
-    jb = join_bytes(tst, dp) / ran
-    jt = tst["join_ms_ran"] / 1e3 / ran
+    kern = {"join_kernel": (join_bytes(tst, dp), tst["join_ms_ran"]),
+            "merge_kernel": (merge_bytes(tst), tst["merge_ms_ran"])}
+    name = max(kern, key=lambda k: kern[k][1])
+    jb = kern[name][0] / ran
+    jt = kern[name][1] / 1e3 / ran
     achieved = jb / jt / 1e9
-    roof = {"kernel": "join_kernel", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+    roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
             "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
             "peak_source": "measured" if peaks else "fallback",
-            "bytes_per_launch": round(jb), "launch_ms": round(jt * 1e3, 4), "launches": ran}
+            "bytes_per_launch": round(jb), "launch_ms": round(jt * 1e3, 4), "launches": ran,
+            "time_share_join_merge": [round(tst["join_ms_ran"], 3), round(tst["merge_ms_ran"], 3)]}
 
     cpu = None
     if not args.no_cpu and ws == 1:

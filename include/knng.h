@@ -56,7 +56,7 @@ extern "C" {
 /* flags for knng_init / knng_build_ex */
 #define KNNG_FLAG_REORDER 0x1u   /* Algorithm 1 (list of the node on spot i) + relabel after iteration 1 */
 #define KNNG_FLAG_REORDER_B 0x2u /* with REORDER: the literal reading (list of node i) */
-#define KNNG_FLAG_TIMING 0x4u    /* record CUDA events around every local-join launch */
+#define KNNG_FLAG_TIMING 0x4u    /* record CUDA events around every local-join and list-merge launch */
 #define KNNG_FLAG_GRAPH 0x8u     /* knng_run: replay the iteration loop as one CUDA graph */
 
 typedef struct knng_ctx knng_ctx;
@@ -77,12 +77,15 @@ typedef struct knng_stats {
     int64_t lock_timeouts;     /* bounded lock waits that gave up (then KNNG_ERR_TIMEOUT) */
     int64_t kernel_launches;   /* kernels this context launched */
     int64_t cand_ids;          /* sampled candidate ids read by the local join */
+    int64_t proposals;         /* proposal keys the local join handed to the list merge */
+    int64_t bucket_overflow;   /* proposals past a full bucket (inserted under a lock) */
     int32_t reordered;         /* 1 once Algorithm 1 relabelled the points */
     int32_t join_launches;     /* local-join launches timed (KNNG_FLAG_TIMING) */
     double join_ms;            /* their summed CUDA-event time */
     int32_t join_ran;          /* timed launches whose iteration ran (not skipped) */
     int32_t reserved;
-    double join_ms_ran;        /* summed time of those launches */
+    double join_ms_ran;        /* summed join-kernel time of those iterations */
+    double merge_ms_ran;       /* summed list-merge-kernel time of those iterations */
 } knng_stats;
 
 /*

@@ -20,6 +20,14 @@ constexpr int kMaxItersArg = 1000;
 
 int rev_capacity(int s) { return 2 * s + 8; }
 
+// proposal bucket per node: twice the (2s)^2 proposals a node receives on
+// average in a dense first iteration, rounded to 32 (overflow goes the locked way)
+int bucket_capacity(int s) {
+    int c = 2 * (2 * s) * (2 * s);
+    c = (c + 31) & ~31;
+    return c < 64 ? 64 : c;
+}
+
 int sample_size(float rho, int K) {
     int s = (int)std::ceil((double)rho * (double)K - 1e-9);
     if (s < 1) s = 1;
@@ -59,7 +67,7 @@ int check_args(int64_t n, int d, int K, float rho, float delta) {
 
 struct knng_ctx {
     int64_t n = 0;
-    int d = 0, dp = 0, nv = 0, K = 0, s = 0, R = 0, cap = 0;
+    int d = 0, dp = 0, nv = 0, K = 0, s = 0, R = 0, cap = 0, pcap = 0;
     float rho = 0, delta = 0;
     uint64_t seed = 0;
     uint32_t flags = 0;
@@ -73,7 +81,8 @@ struct knng_ctx {
     unsigned char *arena = nullptr;
     float *X = nullptr, *X2 = nullptr;
     uint64_t *keys = nullptr, *keys2 = nullptr;
-    int *locks = nullptr, *ibuf = nullptr, *cand = nullptr, *err = nullptr;
+    int *locks = nullptr, *ibuf = nullptr, *cand = nullptr, *err = nullptr, *pcursor = nullptr;
+    uint64_t *pbucket = nullptr;
     int32_t *sigma = nullptr, *sigma_inv = nullptr, *total_perm = nullptr, *total_inv = nullptr;
     long long *stats = nullptr, *it_stats = nullptr;
 
@@ -85,6 +94,8 @@ struct knng_ctx {
         st.X = X;
         st.keys = keys;
         st.locks = locks;
+        st.pcursor = pcursor;
+        st.pbucket = pbucket;
         st.rev_new = ibuf;
         st.rev_old = ibuf + n;
         st.fill_new = ibuf + 2 * n;
@@ -102,6 +113,7 @@ struct knng_ctx {
         st.s = s;
         st.R = R;
         st.cap = cap;
+        st.pcap = pcap;
         st.thr = gate ? thr : -1.0;
         return st;
     }
@@ -122,7 +134,8 @@ int ctx_alloc(knng_ctx *c) {
     const size_t oX2 = reorder ? take(sizeof(float) * n * c->dp) : 0;
     const size_t oK = take(sizeof(uint64_t) * n * c->K);
     const size_t oK2 = reorder ? take(sizeof(uint64_t) * n * c->K) : 0;
-    const size_t oL = take(sizeof(int) * n);
+    const size_t oL = take(sizeof(int) * 2 * n);  // locks, then bucket cursors
+    const size_t oB = take(sizeof(uint64_t) * (size_t)n * c->pcap);
     const size_t oI = take(sizeof(int) * 6 * n);
     const size_t oC = take(sizeof(int) * 2 * (size_t)n * c->cap);
     const size_t oP = reorder ? take(sizeof(int32_t) * 4 * n) : 0;
@@ -140,6 +153,8 @@ int ctx_alloc(knng_ctx *c) {
     c->keys = (uint64_t *)(a + oK);
     c->keys2 = reorder ? (uint64_t *)(a + oK2) : nullptr;
     c->locks = (int *)(a + oL);
+    c->pcursor = c->locks + n;
+    c->pbucket = (uint64_t *)(a + oB);
     c->ibuf = (int *)(a + oI);
     c->cand = (int *)(a + oC);
     if (reorder) {
@@ -152,7 +167,7 @@ int ctx_alloc(knng_ctx *c) {
     c->stats = (long long *)(a + oS);
     c->it_stats = (long long *)(a + oT);
     c->err = (int *)(a + oE);
-    KNNG_TRY(cudaMemsetAsync(c->locks, 0, sizeof(int) * n, c->stream));
+    KNNG_TRY(cudaMemsetAsync(c->locks, 0, sizeof(int) * 2 * n, c->stream));
     KNNG_TRY(cudaMemsetAsync(c->ibuf, 0, sizeof(int) * 6 * n, c->stream));
     KNNG_TRY(cudaMemsetAsync(c->stats, 0, sizeof(long long) * kStatCount, c->stream));
     KNNG_TRY(cudaMemsetAsync(c->it_stats, 0, sizeof(long long) * kItCount * kMaxLocalIters, c->stream));
@@ -193,6 +208,7 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
     c->s = sample_size(rho, K);
     c->R = rev_capacity(c->s);
     c->cap = K + c->R;
+    c->pcap = bucket_capacity(c->s);
     c->rho = rho;
     c->delta = delta;
     c->seed = seed;
@@ -250,18 +266,18 @@ int enqueue_iteration(knng_ctx *c, bool gate) {
     KNNG_TRY(launch_count(st, li, c->stream));
     KNNG_TRY(launch_sample(st, li, it, c->seed, c->stream));
     const bool timing = (c->flags & KNNG_FLAG_TIMING) != 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     if (timing) {
-        cudaEvent_t a, b;
-        KNNG_TRY(cudaEventCreate(&a));
-        KNNG_TRY(cudaEventCreate(&b));
-        c->ev.push_back(a);
-        c->ev.push_back(b);
+        for (auto &e : ev) KNNG_TRY(cudaEventCreate(&e));
+        for (auto &e : ev) c->ev.push_back(e);
         c->ev_li.push_back(li);
-        KNNG_TRY(cudaEventRecord(a, c->stream));
+        KNNG_TRY(cudaEventRecord(ev[0], c->stream));
     }
     KNNG_TRY(launch_join(st, li, c->stream));
-    if (timing) KNNG_TRY(cudaEventRecord(c->ev.back(), c->stream));
-    c->launches += 3;
+    if (timing) KNNG_TRY(cudaEventRecord(ev[1], c->stream));
+    KNNG_TRY(launch_merge(st, li, c->stream));
+    if (timing) KNNG_TRY(cudaEventRecord(ev[2], c->stream));
+    c->launches += 4;
     c->li++;
     c->it_done++;
     if ((c->flags & KNNG_FLAG_REORDER) && !c->reordered && it == 1) {
@@ -491,22 +507,30 @@ int knng_get_stats(knng_ctx *c, knng_stats *out) {
     out->kernel_launches = c->launches;
     out->reordered = c->reordered ? 1 : 0;
     out->cand_ids = 0;
-    for (int i = 0; i < c->li; ++i) out->cand_ids += its[(size_t)i * kItCount + kItCandIds];
+    out->proposals = 0;
+    for (int i = 0; i < c->li; ++i) {
+        out->cand_ids += its[(size_t)i * kItCount + kItCandIds];
+        out->proposals += its[(size_t)i * kItCount + kItProposals];
+    }
     out->join_ms = 0;
     out->join_ms_ran = 0;
-    for (size_t i = 0; i + 1 < c->ev.size(); i += 2) {
-        float ms = 0;
-        if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) {
+    out->merge_ms_ran = 0;
+    for (size_t i = 0; i + 2 < c->ev.size(); i += 3) {
+        float ms = 0, ms2 = 0;
+        if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms2, c->ev[i + 1], c->ev[i + 2]) == cudaSuccess) {
             out->join_ms += ms;
             out->join_launches++;
-            if (its[(size_t)c->ev_li[i / 2] * kItCount + kItRan]) {
+            if (its[(size_t)c->ev_li[i / 3] * kItCount + kItRan]) {
                 out->join_ms_ran += ms;
+                out->merge_ms_ran += ms2;
                 out->join_ran++;
             }
         } else {
             cudaGetLastError();
         }
     }
+    out->bucket_overflow = st[kStatBucketOverflow];
     return KNNG_OK;
 }
 

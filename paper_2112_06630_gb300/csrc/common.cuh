@@ -150,6 +150,7 @@ enum Stat : int {
     kStatSetOverflow,
     kStatLockTimeout,
     kStatInitAttemptsExceeded,
+    kStatBucketOverflow,
     kStatCount
 };
 // Per-iteration counters (index into it_stats[iter * kItCount]).
@@ -161,13 +162,16 @@ enum ItStat : int {
     kItMerges,       // locked merges
     kItInserts,      // insertions (incl. evicted later)
     kItCandIds,      // raw candidate ids read
+    kItProposals,    // proposal keys written to buckets (or inserted past a full one)
     kItCount = 8
 };
 
 struct DevState {
     const float *X;      // n x dp, zero padded
     uint64_t *keys;      // n x K, ascending
-    int *locks;          // n
+    int *locks;          // n, taken only when a proposal bucket is full
+    int *pcursor;        // n, proposals reserved in each node's bucket this iteration
+    uint64_t *pbucket;   // n x pcap proposal keys
     int *rev_new, *rev_old;    // reverse degrees by flag
     int *fill_new, *fill_old;  // reverse candidate fill counters
     int *fwd_new, *fwd_old;    // accepted forward counts
@@ -175,7 +179,7 @@ struct DevState {
     long long *stats;
     long long *it_stats;       // (max_iters + 2) x kItCount
     int64_t n;
-    int dp, nv, K, s, R, cap;
+    int dp, nv, K, s, R, cap, pcap;
     double thr;                // delta * n * K
 };
 

@@ -1,27 +1,34 @@
-// join.cu -- the local join (the paper's Calculation step, Section 2 and
-// Section 3.3) with the list updates, float32 difference-form distances.
+// join.cu -- the local join and the list update (the paper's Calculation
+// step, Section 2 and Section 3.3), float32 difference-form distances.
 //
-// One warp owns one node u at a time (persistent grid-stride loop):
+// Two kernels per iteration, no locks on the common path:
+//
+// join_kernel: one warp owns one node u at a time (persistent grid-stride):
 //   1. read u's sampled candidates (forward part written by u's sampling warp,
 //      reverse part filled by other warps), drop repeats keeping the first
-//      occurrence (new before old), cap the set S at 64;
-//   2. gather the candidate rows into shared memory (padded row stride so
-//      lanes reading different rows hit different banks) and snapshot each
-//      candidate's current worst key;
-//   3. lane i takes target S_i and walks every partner S_j that forms a join
-//      pair with it (both new, or one new and one old); partner rows are read
-//      by all lanes at once (shared-memory broadcast).  A pair whose key
-//      (dist, S_j) beats the snapshot worst of S_i sets bit j of a mask;
-//   4. lanes with a non-empty mask lock S_i's list (bounded wait), load it
-//      into registers, insert the masked partners in order (insertion only if
-//      the key beats the current worst and the id is not listed), write the
-//      list back and unlock.
-// Each unordered pair is evaluated from both ends, so no pairwise matrix is
-// stored and no lane writes another lane's target.  Since every float32
-// distance in the library uses the same arithmetic, a pair always yields the
-// same key and the final lists do not depend on the order in which warps take
-// the locks: each list ends as the K smallest distinct keys of its start
-// entries and all proposals it received.
+//      occurrence (new before old), cap the set S at 64; a node without new
+//      candidates has no join pair and is skipped;
+//   2. gather the candidate rows into shared memory (padded row stride) and
+//      snapshot each candidate's current worst key;
+//   3. enumerate every join pair once -- {p, q} inside new(u) through a
+//      circulant walk (pair (r, r+1+c mod m'), m' = m rounded up to odd, meets
+//      every unordered pair exactly once) and new(u) x old(u) as a rectangle --
+//      with all 32 lanes taking consecutive pairs.  A pair whose key beats the
+//      snapshot worst of an endpoint sets the partner's bit in that endpoint's
+//      64-bit proposal mask (shared-memory atomicOr);
+//   4. lane per target with proposals: one atomicAdd reserves a run in the
+//      target's proposal bucket and the lane writes the keys (recomputing each
+//      pair with the same arithmetic, so the same bits).  A bucket that is
+//      full takes the rest by a locked insertion into the list (bounded spin;
+//      rare).
+// merge_kernel: one warp per node with a non-empty bucket: lane k holds list
+//   entry k; bucket keys arrive 32 at a time, those beating the worst are
+//   inserted one by one with ballots (skip if the id is listed).  The entries
+//   still flagged "inserted in this iteration" at the end are the iteration's
+//   changes for that list.
+// Since every float32 distance in the library uses the same arithmetic, a pair
+// always yields the same key, and each list ends as the K smallest distinct
+// keys of its start entries and all proposals it received, whatever the order.
 #include "internal.h"
 
 namespace knng {
@@ -29,51 +36,87 @@ namespace knng {
 namespace {
 constexpr int kSetMax = 64;
 constexpr int kJoinWarps = 4;
+constexpr int kMergeWarps = 8;
+constexpr int kLockSpins = 1 << 20;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct JoinLayout {
-    int raw_max;     // ints for raw candidate ids
-    int row_stride;  // float4 per staged row
-    size_t per_warp; // bytes
+    int raw_max;      // ints for raw candidate ids
+    int row_stride;   // float4 per staged row
+    size_t off_swk;   // byte offsets inside a warp's region
+    size_t off_rows;
+    size_t per_warp;  // bytes
 };
 
+// per-warp shared memory: raw ids | sid[64] | base[64] | swk[64] | mask[64] | rows[64][rs]
 __host__ __device__ inline JoinLayout join_layout(int cap, int nv, bool rows_smem) {
     JoinLayout L;
     L.raw_max = ((2 * cap + 31) / 32) * 32;
     L.row_stride = (nv % 2 == 0) ? nv + 1 : nv;
-    size_t b = (size_t)L.raw_max * 4 + kSetMax * 4 + kSetMax * 8;
+    size_t b = (size_t)L.raw_max * 4 + kSetMax * 4 * 2;
     b = (b + 15) & ~(size_t)15;
+    L.off_swk = b;
+    b += kSetMax * 8 * 2;
+    b = (b + 15) & ~(size_t)15;
+    L.off_rows = b;
     if (rows_smem) b += (size_t)kSetMax * L.row_stride * 16;
     L.per_warp = b;
     return L;
 }
 
+// q / divisor for q < 2^12 and 2 <= divisor <= 64 given magic = ceil(2^32 /
+// divisor): exact, the rounding error stays below 2^-20.  Divisor 1 (magic
+// would need 33 bits) is passed through.
+__device__ __forceinline__ uint32_t div_small(uint32_t q, uint32_t divisor, uint32_t magic) {
+    return divisor == 1u ? q : __umulhi(q, magic);
+}
+__device__ __forceinline__ uint32_t div_magic(uint32_t divisor) {
+    return divisor > 1u ? (uint32_t)((0x100000000ull + divisor - 1) / divisor) : 0u;
+}
+
+// Insert x into the list held one entry per lane (Lk, lane k = entry k of K,
+// ascending): only if it orders before the worst entry and its id is not
+// listed.  Warp-uniform result: true if inserted.
+__device__ __forceinline__ bool warp_insert(uint64_t &Lk, uint64_t x, int K) {
+    const unsigned lane = lane_id();
+    const bool valid = (int)lane < K;
+    const uint64_t worst = __shfl_sync(kFull, Lk, K - 1);
+    if (x >= worst) return false;
+    if (__ballot_sync(kFull, valid && key_id(Lk) == key_id(x))) return false;
+    const unsigned gt = __ballot_sync(kFull, valid && Lk > x);
+    const int pos = __ffs(gt) - 1;  // first entry ordered after x
+    const uint64_t up = __shfl_up_sync(kFull, Lk, 1);
+    if (valid && (int)lane >= pos) Lk = (int)lane == pos ? x : up;
+    return true;
+}
 }  // namespace
 
-template <int KMAX, bool kRowsSmem>
-__global__ void __launch_bounds__(kJoinWarps * 32) join_kernel(DevState st, int li) {
+template <bool kRowsSmem>
+__global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, int li) {
     if (iteration_skipped(st, li)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long bstat[kItCount];
-    __shared__ long long btimeout;
+    __shared__ long long bovf, btimeout;
     if (threadIdx.x < kItCount) bstat[threadIdx.x] = 0;
-    if (threadIdx.x == 0) btimeout = 0;
+    if (threadIdx.x == 0) bovf = btimeout = 0;
     __syncthreads();
 
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
-    const int K = st.K, R = st.R, cap = st.cap, nv = st.nv;
+    const int K = st.K, R = st.R, cap = st.cap, nv = st.nv, bcap = st.pcap;
     const JoinLayout lay = join_layout(cap, nv, kRowsSmem);
     unsigned char *wbase = smem + (size_t)warp * lay.per_warp;
     int *raw = reinterpret_cast<int *>(wbase);
     int *sid = raw + lay.raw_max;
-    uint64_t *swk = reinterpret_cast<uint64_t *>(sid + kSetMax);
-    float4 *rows = reinterpret_cast<float4 *>(wbase + (((size_t)lay.raw_max * 4 + kSetMax * 12 + 15) & ~(size_t)15));
+    int *base = sid + kSetMax;
+    uint64_t *swk = reinterpret_cast<uint64_t *>(wbase + lay.off_swk);
+    unsigned long long *mask = reinterpret_cast<unsigned long long *>(swk + kSetMax);
+    float4 *rows = reinterpret_cast<float4 *>(wbase + lay.off_rows);
     const int rs = lay.row_stride;
     const float4 *X4 = reinterpret_cast<const float4 *>(st.X);
 
-    long long w_evals = 0, w_gathered = 0, w_candids = 0, w_setovf = 0;
-    long long l_ins = 0, l_evins = 0, l_merges = 0, l_timeouts = 0;
+    long long w_evals = 0, w_gathered = 0, w_candids = 0, w_setovf = 0, w_ovf = 0, w_ins = 0, w_to = 0;
+    long long l_props = 0;  // per lane
 
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -89,6 +132,8 @@ __global__ void __launch_bounds__(kJoinWarps * 32) join_kernel(DevState st, int 
         }
         const int nnew_raw = fn + rn;
         const int total = nnew_raw + fo + ro;
+        w_candids += total;
+        if (nnew_raw == 0) continue;  // no new candidate: no join pair
         for (int idx = lane; idx < total; idx += 32) {
             int v;
             if (idx < fn) v = st.cand_new[cb + idx];
@@ -99,8 +144,8 @@ __global__ void __launch_bounds__(kJoinWarps * 32) join_kernel(DevState st, int 
         }
         __syncwarp();
         int ns = 0, m = 0;
-        for (int base = 0; base < total; base += 32) {
-            const int idx = base + lane;
+        for (int b0 = 0; b0 < total; b0 += 32) {
+            const int idx = b0 + lane;
             bool keep = false;
             int v = -1;
             if (idx < total) {
@@ -123,9 +168,13 @@ __global__ void __launch_bounds__(kJoinWarps * 32) join_kernel(DevState st, int 
             ns = kSetMax;
         }
         m = min(m, ns);
+        const int o = ns - m;
         __syncwarp();
-        // ---- 2. snapshot worst keys, stage rows
-        for (int i = lane; i < ns; i += 32) swk[i] = __ldcg(st.keys + (size_t)sid[i] * K + (K - 1));
+        // ---- 2. snapshot worst keys, clear masks, stage rows
+        for (int i = lane; i < ns; i += 32) {
+            swk[i] = __ldcg(st.keys + (size_t)sid[i] * K + (K - 1));
+            mask[i] = 0ull;
+        }
         if (kRowsSmem) {
             for (int idx = lane; idx < ns * nv; idx += 32) {
                 const int r = idx / nv, c = idx - r * nv;
@@ -133,114 +182,199 @@ __global__ void __launch_bounds__(kJoinWarps * 32) join_kernel(DevState st, int 
             }
         }
         __syncwarp();
-        w_evals += (long long)m * (m - 1) / 2 + (long long)m * (ns - m);
         w_gathered += ns;
-        w_candids += total;
-        // ---- 3./4. lane = target
-        for (int base = 0; base < ns; base += 32) {
-            const int i = base + lane;
-            const bool act = i < ns;
-            const int jend = act ? (i < m ? ns : m) : 0;
-            const int jmax = __reduce_max_sync(kFull, jend);
-            const float4 *own = kRowsSmem ? rows + (act ? i : 0) * rs : X4 + (size_t)sid[act ? i : 0] * nv;
-            const uint64_t wk = act ? swk[i] : 0ull;
-            uint64_t mask = 0;
-            for (int j = 0; j < jmax; ++j) {
-                const float4 *pr = kRowsSmem ? rows + j * rs : X4 + (size_t)sid[j] * nv;
-                const uint32_t vj = (uint32_t)sid[j];
-                if (j < jend && j != i) {
-                    const float dd = l2sq_rows(own, pr, nv);
-                    if (make_key(dd, vj, kFlagNew | kFlagIns) < wk) mask |= 1ull << j;
+        // ---- 3. every join pair once, all lanes busy
+        const int mo = m | 1, half = (mo - 1) >> 1;
+        const uint32_t t1 = (uint32_t)mo * (uint32_t)half;  // circulant slots over new(u)
+        const uint32_t t2 = (uint32_t)m * (uint32_t)o;       // new(u) x old(u)
+        const uint32_t mg1 = div_magic((uint32_t)half), mg2 = div_magic((uint32_t)o);
+        w_evals += (long long)m * (m - 1) / 2 + (long long)m * o;
+        for (uint32_t k = lane; k < t1 + t2; k += 32) {
+            int i, j;
+            if (k < t1) {
+                const uint32_t r = div_small(k, (uint32_t)half, mg1);
+                const uint32_t c = k - r * (uint32_t)half;
+                i = (int)r;
+                j = (int)(r + 1 + c);
+                if (j >= mo) j -= mo;
+                if (i >= m || j >= m) continue;  // the padding slot of an even m
+            } else {
+                const uint32_t q = k - t1;
+                const uint32_t r = div_small(q, (uint32_t)o, mg2);
+                i = (int)r;
+                j = m + (int)(q - r * (uint32_t)o);
+            }
+            const float4 *ri = kRowsSmem ? rows + i * rs : X4 + (size_t)sid[i] * nv;
+            const float4 *rj = kRowsSmem ? rows + j * rs : X4 + (size_t)sid[j] * nv;
+            const float dd = l2sq_rows(ri, rj, nv);
+            if (make_key(dd, (uint32_t)sid[j], kFlagNew | kFlagIns) < swk[i]) atomicOr(&mask[i], 1ull << j);
+            if (make_key(dd, (uint32_t)sid[i], kFlagNew | kFlagIns) < swk[j]) atomicOr(&mask[j], 1ull << i);
+        }
+        __syncwarp();
+        // ---- 4. bucket runs: lane = target; one reservation per target, then
+        //         the lane writes its run (recomputing each pair with the
+        //         arithmetic of step 3, so the keys are bit-identical)
+        unsigned ovf_lo = 0, ovf_hi = 0;  // targets whose run did not fit
+        for (int t = lane; t < ns; t += 32) {
+            const unsigned long long mt = mask[t];
+            const int c = __popcll(mt);
+            if (!c) continue;
+            l_props += c;
+            const uint32_t p = (uint32_t)sid[t];
+            const int b = atomicAdd(st.pcursor + p, c);
+            const int fit = min(c, max(0, bcap - b));
+            const float4 *rt = kRowsSmem ? rows + t * rs : X4 + (size_t)p * nv;
+            uint64_t *bucket = st.pbucket + (size_t)p * bcap + b;
+            unsigned long long mm = mt;
+            for (int r = 0; r < fit; ++r, mm &= mm - 1) {
+                const int j = __ffsll((long long)mm) - 1;
+                const float4 *rj = kRowsSmem ? rows + j * rs : X4 + (size_t)sid[j] * nv;
+                bucket[r] = make_key(l2sq_rows(rt, rj, nv), (uint32_t)sid[j], kFlagNew | kFlagIns);
+            }
+            if (fit < c) {
+                base[t] = fit;  // proposals of t from rank `fit` on still to insert
+                if (t < 32) ovf_lo |= 1u << t;
+                else ovf_hi |= 1u << (t - 32);
+            }
+        }
+        ovf_lo = __reduce_or_sync(kFull, ovf_lo);
+        ovf_hi = __reduce_or_sync(kFull, ovf_hi);
+        __syncwarp();
+        // full buckets (rare): insert the rest straight into the list, locked
+        for (unsigned long long om = (unsigned long long)ovf_lo | ((unsigned long long)ovf_hi << 32); om;
+             om &= om - 1) {
+            const int t = __ffsll((long long)om) - 1;
+            const uint32_t p = (uint32_t)sid[t];
+            // partner bits of t from rank base[t] on
+            unsigned long long rest = mask[t];
+            for (int r = 0; r < base[t]; ++r) rest &= rest - 1;
+            w_ovf += __popcll(rest);
+            bool got = false;
+            if (lane == 0) {
+                for (int spin = 0; spin < kLockSpins; ++spin) {
+                    if (atomicCAS(st.locks + p, 0, 1) == 0) {
+                        got = true;
+                        break;
+                    }
+                    __nanosleep(spin < 64 ? 64 : 512);
+                }
+                if (got) __threadfence();
+            }
+            got = __shfl_sync(kFull, got, 0);
+            if (!got) {
+                ++w_to;
+                continue;
+            }
+            const float4 *rt = kRowsSmem ? rows + t * rs : X4 + (size_t)p * nv;
+            uint64_t xs[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = (int)lane + 32 * h;
+                xs[h] = kKeyEmpty;
+                if ((rest >> j) & 1ull) {
+                    const float4 *rj = kRowsSmem ? rows + j * rs : X4 + (size_t)sid[j] * nv;
+                    xs[h] = make_key(l2sq_rows(rt, rj, nv), (uint32_t)sid[j], kFlagNew | kFlagIns);
                 }
             }
-            if (mask) {
-                const uint32_t p = (uint32_t)sid[i];
-                int *lk = st.locks + p;
-                if (lock_acquire(lk)) {
-                    // right-aligned register list: slots [KMAX-K, KMAX) hold the
-                    // list, slots below it hold 0, which orders before every
-                    // proposal (proposal keys carry flag bits, so they are > 0);
-                    // the worst entry is always L[KMAX-1].
-                    const int off = KMAX - K;
-                    uint64_t *row = st.keys + (size_t)p * K - off;
-                    uint64_t L[KMAX];
-#pragma unroll
-                    for (int k = 0; k < KMAX; ++k) L[k] = k >= off ? __ldcg(row + k) : 0ull;
-                    bool changed = false;
-                    while (mask) {
-                        const int j = __ffsll((long long)mask) - 1;
-                        mask &= mask - 1;
-                        const uint32_t vj = (uint32_t)sid[j];
-                        const float4 *pr = kRowsSmem ? rows + j * rs : X4 + (size_t)vj * nv;
-                        const uint64_t x = make_key(l2sq_rows(own, pr, nv), vj, kFlagNew | kFlagIns);
-                        if (x >= L[KMAX - 1]) continue;
-                        bool dup = false;
-#pragma unroll
-                        for (int k = 0; k < KMAX; ++k) dup |= (k >= off) && key_id(L[k]) == vj;
-                        if (dup) continue;
-                        if (L[KMAX - 1] & kFlagIns) ++l_evins;
-                        ++l_ins;
-#pragma unroll
-                        for (int k = KMAX - 1; k >= 1; --k) {
-                            const uint64_t lo = L[k] < x ? L[k] : x;
-                            L[k] = lo > L[k - 1] ? lo : L[k - 1];
-                        }
-                        L[0] = L[0] < x ? L[0] : x;
-                        changed = true;
-                    }
-                    if (changed) {
-#pragma unroll
-                        for (int k = 0; k < KMAX; ++k)
-                            if (k >= off) __stcg(row + k, L[k]);
-                    }
-                    lock_release(lk);
-                    ++l_merges;
-                } else {
-                    ++l_timeouts;
-                }
+            uint64_t *row = st.keys + (size_t)p * K;
+            uint64_t Lk = (int)lane < K ? __ldcg(row + lane) : kKeyEmpty;
+            for (unsigned long long mm = rest; mm; mm &= mm - 1) {
+                const int j = __ffsll((long long)mm) - 1;
+                const uint64_t xa = __shfl_sync(kFull, xs[0], j & 31), xb = __shfl_sync(kFull, xs[1], j & 31);
+                w_ins += warp_insert(Lk, j < 32 ? xa : xb, K);
             }
+            if ((int)lane < K) __stcg(row + lane, Lk);
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) atomicExch(st.locks + p, 0);
         }
         __syncwarp();
     }
-    // ---- counters: warp -> block -> global
-    l_ins = warp_sum(l_ins);
-    l_evins = warp_sum(l_evins);
-    l_merges = warp_sum(l_merges);
-    l_timeouts = warp_sum(l_timeouts);
+    // ---- counters (w_* are warp-uniform): warp -> block -> global
+    const long long w_props = warp_sum(l_props);
     if (lane == 0) {
+        atomic_add_ll(&bstat[kItProposals], w_props);
         atomic_add_ll(&bstat[kItEvals], w_evals);
         atomic_add_ll(&bstat[kItGathered], w_gathered);
         atomic_add_ll(&bstat[kItCandIds], w_candids);
-        atomic_add_ll(&bstat[kItMerges], l_merges);
-        atomic_add_ll(&bstat[kItInserts], l_ins);
-        atomic_add_ll(&bstat[kItChanges], l_ins - l_evins);
-        atomic_add_ll(&btimeout, l_timeouts);
+        atomic_add_ll(&bstat[kItInserts], w_ins);
+        atomic_add_ll(&bovf, w_ovf);
+        atomic_add_ll(&btimeout, w_to);
         if (w_setovf) atomic_add_ll(&st.stats[kStatSetOverflow], w_setovf);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         long long *its = st.it_stats + (size_t)li * kItCount;
         its[kItRan] = 1;
-        atomic_add_ll(&its[kItChanges], bstat[kItChanges]);
         atomic_add_ll(&its[kItEvals], bstat[kItEvals]);
         atomic_add_ll(&its[kItGathered], bstat[kItGathered]);
         atomic_add_ll(&its[kItCandIds], bstat[kItCandIds]);
-        atomic_add_ll(&its[kItMerges], bstat[kItMerges]);
         atomic_add_ll(&its[kItInserts], bstat[kItInserts]);
+        atomic_add_ll(&its[kItProposals], bstat[kItProposals]);
         atomic_add_ll(&st.stats[kStatEvals], bstat[kItEvals]);
         atomic_add_ll(&st.stats[kStatInserts], bstat[kItInserts]);
-        atomic_add_ll(&st.stats[kStatMerges], bstat[kItMerges]);
         atomic_add_ll(&st.stats[kStatGathered], bstat[kItGathered]);
+        if (bovf) atomic_add_ll(&st.stats[kStatBucketOverflow], bovf);
         if (btimeout) atomic_add_ll(&st.stats[kStatLockTimeout], btimeout);
     }
 }
 
+// One warp per node with proposals: merge its bucket into its list.
+__global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(DevState st, int li) {
+    if (iteration_skipped(st, li)) return;
+    __shared__ long long bstat[3];
+    if (threadIdx.x < 3) bstat[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned lane = lane_id();
+    const int K = st.K, bcap = st.pcap;
+    const bool valid = (int)lane < K;
+    long long w_ins = 0, w_changes = 0, w_merges = 0;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long p = gw; p < st.n; p += nw) {
+        const int cnt_all = st.pcursor[p];
+        if (cnt_all == 0) continue;
+        __syncwarp();
+        if (lane == 0) st.pcursor[p] = 0;
+        const int cnt = min(cnt_all, bcap);
+        uint64_t *row = st.keys + (size_t)p * K;
+        const uint64_t *bucket = st.pbucket + (size_t)p * bcap;
+        uint64_t Lk = valid ? row[lane] : kKeyEmpty;
+        int ins = 0;
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            const uint64_t x = c0 + (int)lane < cnt ? __ldcs(bucket + c0 + lane) : kKeyEmpty;
+            unsigned cand = __ballot_sync(kFull, x < __shfl_sync(kFull, Lk, K - 1));
+            for (; cand; cand &= cand - 1) ins += warp_insert(Lk, __shfl_sync(kFull, x, __ffs(cand) - 1), K);
+        }
+        // entries flagged "inserted in this iteration" that are still listed
+        // (the sampling pass cleared that flag everywhere before the join)
+        w_changes += __popc(__ballot_sync(kFull, valid && (Lk & kFlagIns)));
+        if (ins && valid) row[lane] = Lk;
+        w_ins += ins;
+        ++w_merges;
+    }
+    if (lane == 0) {
+        atomic_add_ll(&bstat[0], w_ins);
+        atomic_add_ll(&bstat[1], w_changes);
+        atomic_add_ll(&bstat[2], w_merges);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long *its = st.it_stats + (size_t)li * kItCount;
+        atomic_add_ll(&its[kItInserts], bstat[0]);
+        atomic_add_ll(&its[kItChanges], bstat[1]);
+        atomic_add_ll(&its[kItMerges], bstat[2]);
+        atomic_add_ll(&st.stats[kStatInserts], bstat[0]);
+        atomic_add_ll(&st.stats[kStatMerges], bstat[2]);
+    }
+}
+
 namespace {
-template <int KMAX, bool S>
+template <bool S>
 cudaError_t launch_join_t(const DevState &st, int li, cudaStream_t s) {
     const JoinLayout lay = join_layout(st.cap, st.nv, S);
     const size_t dyn = lay.per_warp * kJoinWarps;
-    auto kern = join_kernel<KMAX, S>;
+    auto kern = join_kernel<S>;
     static bool opted_in = false;  // allow up to the per-block maximum once
     if (!opted_in) {
         int dev = 0, mx = 0;
@@ -255,20 +389,18 @@ cudaError_t launch_join_t(const DevState &st, int li, cudaStream_t s) {
     kern<<<grid, kJoinWarps * 32, dyn, s>>>(st, li);
     return cudaGetLastError();
 }
-
-template <int KMAX>
-cudaError_t launch_join_k(const DevState &st, int li, cudaStream_t s) {
-    const JoinLayout lay = join_layout(st.cap, st.nv, true);
-    if (lay.per_warp * kJoinWarps <= 110 * 1024) return launch_join_t<KMAX, true>(st, li, s);
-    return launch_join_t<KMAX, false>(st, li, s);
-}
 }  // namespace
 
 cudaError_t launch_join(const DevState &st, int li, cudaStream_t s) {
-    if (st.K <= 8) return launch_join_k<8>(st, li, s);
-    if (st.K <= 16) return launch_join_k<16>(st, li, s);
-    if (st.K <= 24) return launch_join_k<24>(st, li, s);
-    return launch_join_k<32>(st, li, s);
+    const JoinLayout lay = join_layout(st.cap, st.nv, true);
+    if (lay.per_warp * kJoinWarps <= 110 * 1024) return launch_join_t<true>(st, li, s);
+    return launch_join_t<false>(st, li, s);
+}
+
+cudaError_t launch_merge(const DevState &st, int li, cudaStream_t s) {
+    const int grid = grid_for((const void *)merge_kernel, kMergeWarps * 32, 0);
+    merge_kernel<<<grid, kMergeWarps * 32, 0, s>>>(st, li);
+    return cudaGetLastError();
 }
 
 }  // namespace knng
