@@ -35,6 +35,7 @@ namespace knng {
 
 namespace {
 constexpr int kSetMax = 64;
+constexpr int kHashBits = 8;  // 256-slot hash set for repeat removal (at most 2 * (32 + 72) ids)
 constexpr int kJoinWarps = 4;
 constexpr int kMergeWarps = 8;
 constexpr int kLockSpins = 1 << 20;
@@ -48,19 +49,19 @@ struct JoinLayout {
     size_t per_warp;  // bytes
 };
 
-// per-warp shared memory: raw ids | sid[64] | base[64] | swk[64] | mask[64] | rows[64][rs]
+// per-warp shared memory: sid[64] | base[64] | swk[64] | mask[64] | scratch
+// where scratch holds the raw candidate ids and the hash set until repeats
+// are removed, and the staged rows[64][rs] afterwards
 __host__ __device__ inline JoinLayout join_layout(int cap, int nv, bool rows_smem) {
     JoinLayout L;
     L.raw_max = ((2 * cap + 31) / 32) * 32;
     L.row_stride = (nv % 2 == 0) ? nv + 1 : nv;
-    size_t b = (size_t)L.raw_max * 4 + kSetMax * 4 * 2;
-    b = (b + 15) & ~(size_t)15;
-    L.off_swk = b;
-    b += kSetMax * 8 * 2;
-    b = (b + 15) & ~(size_t)15;
-    L.off_rows = b;
-    if (rows_smem) b += (size_t)kSetMax * L.row_stride * 16;
-    L.per_warp = b;
+    L.off_swk = kSetMax * 4 * 2;
+    L.off_rows = L.off_swk + kSetMax * 8 * 2;
+    const size_t dedup = (size_t)L.raw_max * 4 + (4u << kHashBits);
+    const size_t rows = rows_smem ? (size_t)kSetMax * L.row_stride * 16 : 0;
+    L.per_warp = L.off_rows + (dedup > rows ? dedup : rows);
+    L.per_warp = (L.per_warp + 15) & ~(size_t)15;
     return L;
 }
 
@@ -106,12 +107,13 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
     const int K = st.K, R = st.R, cap = st.cap, nv = st.nv, bcap = st.pcap;
     const JoinLayout lay = join_layout(cap, nv, kRowsSmem);
     unsigned char *wbase = smem + (size_t)warp * lay.per_warp;
-    int *raw = reinterpret_cast<int *>(wbase);
-    int *sid = raw + lay.raw_max;
+    int *sid = reinterpret_cast<int *>(wbase);
     int *base = sid + kSetMax;
     uint64_t *swk = reinterpret_cast<uint64_t *>(wbase + lay.off_swk);
     unsigned long long *mask = reinterpret_cast<unsigned long long *>(swk + kSetMax);
     float4 *rows = reinterpret_cast<float4 *>(wbase + lay.off_rows);
+    int *hset = reinterpret_cast<int *>(wbase + lay.off_rows);  // aliases rows until they are staged
+    int *raw = hset + (1 << kHashBits);
     const int rs = lay.row_stride;
     const float4 *X4 = reinterpret_cast<const float4 *>(st.X);
 
@@ -143,25 +145,38 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
             raw[idx] = v;
         }
         __syncwarp();
+        for (int i = lane; i < (1 << kHashBits); i += 32) hset[i] = -1;
+        __syncwarp();
+        // repeats removed with a shared-memory hash set: new entries first, so
+        // an id that is both new and old stays new; of repeats of one kind the
+        // copy whose insertion wins stays (the set does not depend on which)
         int ns = 0, m = 0;
-        for (int b0 = 0; b0 < total; b0 += 32) {
-            const int idx = b0 + lane;
-            bool keep = false;
-            int v = -1;
-            if (idx < total) {
-                v = raw[idx];
-                keep = true;
-                for (int k = 0; k < idx; ++k)
-                    if (raw[k] == v) {
-                        keep = false;
-                        break;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int lo_i = pass ? nnew_raw : 0, hi_i = pass ? total : nnew_raw;
+            for (int b0 = lo_i; b0 < hi_i; b0 += 32) {
+                const int idx = b0 + lane;
+                bool keep = false;
+                int v = -1;
+                if (idx < hi_i) {
+                    v = raw[idx];
+                    unsigned h = ((unsigned)v * 0x9E3779B1u) >> (32 - kHashBits);
+                    for (int probe = 0; probe < (1 << kHashBits); ++probe) {
+                        const int prev = atomicCAS(hset + h, -1, v);
+                        if (prev == -1) {
+                            keep = true;
+                            break;
+                        }
+                        if (prev == v) break;
+                        h = (h + 1) & ((1u << kHashBits) - 1);
                     }
+                }
+                const unsigned km = __ballot_sync(kFull, keep);
+                const int pos = ns + __popc(km & lanemask_lt());
+                if (keep && pos < kSetMax) sid[pos] = v;
+                if (!pass) m += __popc(km);
+                ns += __popc(km);
             }
-            const unsigned km = __ballot_sync(kFull, keep);
-            const int pos = ns + __popc(km & lanemask_lt());
-            if (keep && pos < kSetMax) sid[pos] = v;
-            m += __popc(__ballot_sync(kFull, keep && idx < nnew_raw));
-            ns += __popc(km);
+            __syncwarp();
         }
         if (ns > kSetMax) {
             w_setovf += ns - kSetMax;
@@ -343,7 +358,22 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(DevState st, in
         int ins = 0;
         for (int c0 = 0; c0 < cnt; c0 += 32) {
             const uint64_t x = c0 + (int)lane < cnt ? __ldcs(bucket + c0 + lane) : kKeyEmpty;
-            unsigned cand = __ballot_sync(kFull, x < __shfl_sync(kFull, Lk, K - 1));
+            // drop, in parallel, keys that cannot enter: not before the worst,
+            // or already listed (a pair has one key, so "listed" is "the same
+            // (dist, id) at its lower bound"; binary search over the lanes)
+            const uint64_t xo = key_order(x);
+            int lo = 0, hi = K - 1;
+#pragma unroll
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (lo + hi) >> 1;
+                const uint64_t lm = __shfl_sync(kFull, Lk, mid);
+                if (lo < hi) {
+                    if (key_order(lm) < xo) lo = mid + 1;
+                    else hi = mid;
+                }
+            }
+            const bool listed = key_order(__shfl_sync(kFull, Lk, lo)) == xo;
+            unsigned cand = __ballot_sync(kFull, x < __shfl_sync(kFull, Lk, K - 1) && !listed);
             for (; cand; cand &= cand - 1) ins += warp_insert(Lk, __shfl_sync(kFull, x, __ffs(cand) - 1), K);
         }
         // entries flagged "inserted in this iteration" that are still listed
