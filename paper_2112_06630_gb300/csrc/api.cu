@@ -4,6 +4,7 @@
 // kernel launch on the caller's stream.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -19,14 +20,6 @@ constexpr int kMaxLocalIters = 1024;
 constexpr int kMaxItersArg = 1000;
 
 int rev_capacity(int s) { return 2 * s + 8; }
-
-// proposal bucket per node: twice the (2s)^2 proposals a node receives on
-// average in a dense first iteration, rounded to 32 (overflow goes the locked way)
-int bucket_capacity(int s) {
-    int c = 2 * (2 * s) * (2 * s);
-    c = (c + 31) & ~31;
-    return c < 64 ? 64 : c;
-}
 
 int sample_size(float rho, int K) {
     int s = (int)std::ceil((double)rho * (double)K - 1e-9);
@@ -67,7 +60,7 @@ int check_args(int64_t n, int d, int K, float rho, float delta) {
 
 struct knng_ctx {
     int64_t n = 0;
-    int d = 0, dp = 0, nv = 0, K = 0, s = 0, R = 0, cap = 0, pcap = 0;
+    int d = 0, dp = 0, nv = 0, K = 0, s = 0, R = 0, cap = 0, pool_chunks = 0;
     float rho = 0, delta = 0;
     uint64_t seed = 0;
     uint32_t flags = 0;
@@ -82,7 +75,8 @@ struct knng_ctx {
     float *X = nullptr, *X2 = nullptr;
     uint64_t *keys = nullptr, *keys2 = nullptr;
     int *locks = nullptr, *ibuf = nullptr, *cand = nullptr, *err = nullptr, *pcursor = nullptr;
-    uint64_t *pbucket = nullptr;
+    int *pchunk = nullptr, *pool_next = nullptr;
+    uint64_t *pbucket = nullptr, *ppool = nullptr;
     int32_t *sigma = nullptr, *sigma_inv = nullptr, *total_perm = nullptr, *total_inv = nullptr;
     long long *stats = nullptr, *it_stats = nullptr;
 
@@ -96,6 +90,10 @@ struct knng_ctx {
         st.locks = locks;
         st.pcursor = pcursor;
         st.pbucket = pbucket;
+        st.pchunk = pchunk;
+        st.ppool = ppool;
+        st.pool_next = pool_next;
+        st.pool_chunks = pool_chunks;
         st.rev_new = ibuf;
         st.rev_old = ibuf + n;
         st.fill_new = ibuf + 2 * n;
@@ -113,7 +111,6 @@ struct knng_ctx {
         st.s = s;
         st.R = R;
         st.cap = cap;
-        st.pcap = pcap;
         st.thr = gate ? thr : -1.0;
         return st;
     }
@@ -134,8 +131,11 @@ int ctx_alloc(knng_ctx *c) {
     const size_t oX2 = reorder ? take(sizeof(float) * n * c->dp) : 0;
     const size_t oK = take(sizeof(uint64_t) * n * c->K);
     const size_t oK2 = reorder ? take(sizeof(uint64_t) * n * c->K) : 0;
-    const size_t oL = take(sizeof(int) * 2 * n);  // locks, then bucket cursors
-    const size_t oB = take(sizeof(uint64_t) * (size_t)n * c->pcap);
+    // locks | bucket cursors | bucket chunk tables | pool cursor
+    const size_t nint = (size_t)n * (2 + kBucketChunks) + 1;
+    const size_t oL = take(sizeof(int) * nint);
+    const size_t oB = take(sizeof(uint64_t) * (size_t)n * kBucketRun);
+    const size_t oQ = take(sizeof(uint64_t) * (size_t)c->pool_chunks * kBucketRun);
     const size_t oI = take(sizeof(int) * 6 * n);
     const size_t oC = take(sizeof(int) * 2 * (size_t)n * c->cap);
     const size_t oP = reorder ? take(sizeof(int32_t) * 4 * n) : 0;
@@ -154,7 +154,10 @@ int ctx_alloc(knng_ctx *c) {
     c->keys2 = reorder ? (uint64_t *)(a + oK2) : nullptr;
     c->locks = (int *)(a + oL);
     c->pcursor = c->locks + n;
+    c->pchunk = c->locks + 2 * n;
+    c->pool_next = c->pchunk + (size_t)n * kBucketChunks;
     c->pbucket = (uint64_t *)(a + oB);
+    c->ppool = (uint64_t *)(a + oQ);
     c->ibuf = (int *)(a + oI);
     c->cand = (int *)(a + oC);
     if (reorder) {
@@ -167,7 +170,7 @@ int ctx_alloc(knng_ctx *c) {
     c->stats = (long long *)(a + oS);
     c->it_stats = (long long *)(a + oT);
     c->err = (int *)(a + oE);
-    KNNG_TRY(cudaMemsetAsync(c->locks, 0, sizeof(int) * 2 * n, c->stream));
+    KNNG_TRY(cudaMemsetAsync(c->locks, 0, sizeof(int) * nint, c->stream));
     KNNG_TRY(cudaMemsetAsync(c->ibuf, 0, sizeof(int) * 6 * n, c->stream));
     KNNG_TRY(cudaMemsetAsync(c->stats, 0, sizeof(long long) * kStatCount, c->stream));
     KNNG_TRY(cudaMemsetAsync(c->it_stats, 0, sizeof(long long) * kItCount * kMaxLocalIters, c->stream));
@@ -208,7 +211,12 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
     c->s = sample_size(rho, K);
     c->R = rev_capacity(c->s);
     c->cap = K + c->R;
-    c->pcap = bucket_capacity(c->s);
+    // bucket pool: two 256-key runs per node on top of the inline run (the
+    // first, dense iteration averages about (2s)^2 proposals per node)
+    c->pool_chunks = (int)std::min<int64_t>(2 * n + 4096, (int64_t)1 << 30);
+    // test hook: a smaller pool drives proposals through the poisoned-run and
+    // locked-insertion paths
+    if (const char *e = std::getenv("KNNG_TEST_BUCKET_POOL_CHUNKS")) c->pool_chunks = std::max(1, std::atoi(e));
     c->rho = rho;
     c->delta = delta;
     c->seed = seed;

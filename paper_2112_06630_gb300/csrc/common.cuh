@@ -171,7 +171,11 @@ struct DevState {
     uint64_t *keys;      // n x K, ascending
     int *locks;          // n, taken only when a proposal bucket is full
     int *pcursor;        // n, proposals reserved in each node's bucket this iteration
-    uint64_t *pbucket;   // n x pcap proposal keys
+    uint64_t *pbucket;   // n x kBucketRun proposal keys (the first run of every bucket)
+    int *pchunk;         // n x kBucketChunks: pool chunk + 1 of the bucket's further runs, 0 = none
+    uint64_t *ppool;     // pool_chunks x kBucketRun keys
+    int *pool_next;      // next free pool chunk (restarted every iteration)
+    int pool_chunks;
     int *rev_new, *rev_old;    // reverse degrees by flag
     int *fill_new, *fill_old;  // reverse candidate fill counters
     int *fwd_new, *fwd_old;    // accepted forward counts
@@ -179,9 +183,23 @@ struct DevState {
     long long *stats;
     long long *it_stats;       // (max_iters + 2) x kItCount
     int64_t n;
-    int dp, nv, K, s, R, cap, pcap;
+    int dp, nv, K, s, R, cap;
     double thr;                // delta * n * K
 };
+
+// Proposal buckets: run 0 of node p is inline (pbucket), runs 1..15 are pool
+// chunks claimed on demand with a CAS (a lane that loses the race uses the
+// winner's chunk; its own stays unused until the pool restarts).  A run whose
+// chunk cannot be claimed (pool spent) is poisoned for the iteration.
+constexpr int kBucketRunBits = 8;
+constexpr int kBucketRun = 1 << kBucketRunBits;
+constexpr int kBucketChunks = 15;
+constexpr int kBucketMax = kBucketRun * (kBucketChunks + 1);
+constexpr int kChunkPoison = -1;
+
+// Slot of proposal number `pos` of node p, or nullptr when the bucket or the
+// pool is exhausted (the caller then inserts into the list under its lock).
+__device__ __forceinline__ uint64_t *bucket_slot(const DevState &st, uint32_t p, int pos);
 
 // True when iteration `it` must not run because an earlier one converged.
 __device__ __forceinline__ bool iteration_skipped(const DevState &st, int it) {
@@ -190,4 +208,26 @@ __device__ __forceinline__ bool iteration_skipped(const DevState &st, int it) {
     return (double)prev[kItChanges] < st.thr;
 }
 
+}  // namespace knng
+
+namespace knng {
+__device__ __forceinline__ uint64_t *bucket_slot(const DevState &st, uint32_t p, int pos) {
+    const int k = pos >> kBucketRunBits, off = pos & (kBucketRun - 1);
+    if (k == 0) return st.pbucket + ((size_t)p << kBucketRunBits) + off;
+    if (k > kBucketChunks) return nullptr;
+    int *ent = st.pchunk + (size_t)p * kBucketChunks + (k - 1);
+    int c = *reinterpret_cast<volatile int *>(ent);
+    if (c == 0) {
+        // claim a chunk; with the pool spent, install the poison mark instead,
+        // so that no warp can install a chunk for this run afterwards and all
+        // of the run's proposals take the locked way (no unwritten slot is
+        // ever read by the merge)
+        const int fresh = atomicAdd(st.pool_next, 1);
+        const int want = fresh < st.pool_chunks ? fresh + 1 : kChunkPoison;
+        const int old = atomicCAS(ent, 0, want);
+        c = old ? old : want;
+    }
+    if (c == kChunkPoison) return nullptr;
+    return st.ppool + ((size_t)(c - 1) << kBucketRunBits) + off;
+}
 }  // namespace knng

@@ -20,7 +20,8 @@
 //      target's proposal bucket and the lane writes the keys (recomputing each
 //      pair with the same arithmetic, so the same bits).  A bucket that is
 //      full takes the rest by a locked insertion into the list (bounded spin;
-//      rare).
+//      rare).  A bucket is a 256-key run per node plus up to 15 runs claimed
+//      from a pool on demand, so hub nodes hold up to 4,096 proposals.
 // merge_kernel: one warp per node with a non-empty bucket: lane k holds list
 //   entry k; bucket keys arrive 32 at a time, those beating the worst are
 //   inserted one by one with ballots (skip if the id is listed).  The entries
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
 
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
-    const int K = st.K, R = st.R, cap = st.cap, nv = st.nv, bcap = st.pcap;
+    const int K = st.K, R = st.R, cap = st.cap, nv = st.nv;
     const JoinLayout lay = join_layout(cap, nv, kRowsSmem);
     unsigned char *wbase = smem + (size_t)warp * lay.per_warp;
     int *sid = reinterpret_cast<int *>(wbase);
@@ -237,14 +238,18 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
             l_props += c;
             const uint32_t p = (uint32_t)sid[t];
             const int b = atomicAdd(st.pcursor + p, c);
-            const int fit = min(c, max(0, bcap - b));
             const float4 *rt = kRowsSmem ? rows + t * rs : X4 + (size_t)p * nv;
-            uint64_t *bucket = st.pbucket + (size_t)p * bcap + b;
             unsigned long long mm = mt;
-            for (int r = 0; r < fit; ++r, mm &= mm - 1) {
+            int fit = 0;
+            uint64_t *slot = nullptr;
+            for (; fit < c; ++fit, mm &= mm - 1) {
+                const int pos = b + fit;
+                if (fit == 0 || (pos & (kBucketRun - 1)) == 0) slot = bucket_slot(st, p, pos);
+                else ++slot;
+                if (!slot) break;
                 const int j = __ffsll((long long)mm) - 1;
                 const float4 *rj = kRowsSmem ? rows + j * rs : X4 + (size_t)sid[j] * nv;
-                bucket[r] = make_key(l2sq_rows(rt, rj, nv), (uint32_t)sid[j], kFlagNew | kFlagIns);
+                *slot = make_key(l2sq_rows(rt, rj, nv), (uint32_t)sid[j], kFlagNew | kFlagIns);
             }
             if (fit < c) {
                 base[t] = fit;  // proposals of t from rank `fit` on still to insert
@@ -341,7 +346,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(DevState st, in
     if (threadIdx.x < 3) bstat[threadIdx.x] = 0;
     __syncthreads();
     const unsigned lane = lane_id();
-    const int K = st.K, bcap = st.pcap;
+    const int K = st.K;
     const bool valid = (int)lane < K;
     long long w_ins = 0, w_changes = 0, w_merges = 0;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -351,13 +356,25 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(DevState st, in
         if (cnt_all == 0) continue;
         __syncwarp();
         if (lane == 0) st.pcursor[p] = 0;
-        const int cnt = min(cnt_all, bcap);
+        const int cnt = min(cnt_all, kBucketMax);
         uint64_t *row = st.keys + (size_t)p * K;
-        const uint64_t *bucket = st.pbucket + (size_t)p * bcap;
+        int *chunks = st.pchunk + (size_t)p * kBucketChunks;
         uint64_t Lk = valid ? row[lane] : kKeyEmpty;
         int ins = 0;
+        const uint64_t *run = st.pbucket + ((size_t)p << kBucketRunBits);
         for (int c0 = 0; c0 < cnt; c0 += 32) {
-            const uint64_t x = c0 + (int)lane < cnt ? __ldcs(bucket + c0 + lane) : kKeyEmpty;
+            // runs are multiples of 32 keys: a batch of 32 never straddles two
+            const int k = c0 >> kBucketRunBits;
+            if (k > 0 && (c0 & (kBucketRun - 1)) == 0) {
+                const int ch = chunks[k - 1];
+                __syncwarp();
+                if (lane == 0) chunks[k - 1] = 0;
+                // no chunk (or poisoned): these proposals went the locked way
+                run = ch > 0 ? st.ppool + ((size_t)(ch - 1) << kBucketRunBits) : nullptr;
+            }
+            if (!run) continue;
+            const int off = c0 & (kBucketRun - 1);
+            const uint64_t x = c0 + (int)lane < cnt ? __ldcs(run + off + lane) : kKeyEmpty;
             // drop, in parallel, keys that cannot enter: not before the worst,
             // or already listed (a pair has one key, so "listed" is "the same
             // (dist, id) at its lower bound"; binary search over the lanes)

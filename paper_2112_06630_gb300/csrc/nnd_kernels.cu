@@ -148,6 +148,7 @@ __global__ void count_kernel(DevState st, int li) {
         st.fill_new[u] = 0;
         st.fill_old[u] = 0;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *st.pool_next = 0;  // bucket pool restarts
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         uint64_t key = st.keys[e];
         uint32_t v = key_id(key);

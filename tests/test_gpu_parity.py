@@ -130,6 +130,28 @@ def test_one_iteration_matches_oracle_bit_exact(n, d, K, rho, hi):
     assert stats["dist_evals"] == r["evals"]
 
 
+@pytest.mark.parametrize("pool", ["1", "40"])
+def test_bucket_overflow_paths_match_oracle_bit_exact(pool, monkeypatch):
+    """A (test-only) tiny proposal pool forces runs past the first 256 keys of
+    a bucket onto poisoned runs and locked list insertions; the lists must
+    still equal the oracle's."""
+    monkeypatch.setenv("KNNG_TEST_BUCKET_POOL_CHUNKS", pool)
+    n, d, K, rho, hi = 1800, 3, 16, 0.5, 6
+    x = _int_data(n, d, hi, seed=n)
+    ids0, new0 = workloads.random_graph(n, K, seed=n + 1, p_new=0.6)
+    with knng.Context(_cuda(x), K, rho=rho, seed=11, graph=(ids0, new0), iter=0) as c:
+        conv, ch = c.iterate()
+        gi, gd, gf = c.state()
+        stats = c.stats()
+    st = oracle.State(x, K, rho, seed=11)
+    st.init_graph(ids0, new0, 0)
+    r = st.iterate()
+    assert stats["bucket_overflow"] > 0 and stats["lock_timeouts"] == 0
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    assert ch == r["changes"]
+
+
 def test_several_iterations_match_oracle_bit_exact():
     n, d, K, rho = 4000, 8, 12, 0.5
     x = _int_data(n, d, 10, seed=5)
