@@ -58,6 +58,8 @@ extern "C" {
 #define KNNG_FLAG_REORDER_B 0x2u /* with REORDER: the literal reading (list of node i) */
 #define KNNG_FLAG_TIMING 0x4u    /* record CUDA events around every local-join and list-merge launch */
 #define KNNG_FLAG_GRAPH 0x8u     /* knng_run: replay the iteration loop as one CUDA graph */
+#define KNNG_FLAG_BF16 0x10u     /* d >= 64: local-join dots in bf16 on the tensor cores (float32
+                                    accumulate, |x|^2+|y|^2-2x.y); output re-ranked in float32 */
 
 typedef struct knng_ctx knng_ctx;
 

@@ -18,13 +18,14 @@ from . import build as _build
 
 __all__ = [
     "KnngError", "Stats", "Context", "knng_build", "knng_bruteforce", "lib_path",
-    "FLAG_REORDER", "FLAG_REORDER_B", "FLAG_TIMING", "FLAG_GRAPH", "version", "strerror", "load",
+    "FLAG_REORDER", "FLAG_REORDER_B", "FLAG_TIMING", "FLAG_GRAPH", "FLAG_BF16", "version", "strerror", "load",
 ]
 
 FLAG_REORDER = 0x1
 FLAG_REORDER_B = 0x2
 FLAG_TIMING = 0x4
 FLAG_GRAPH = 0x8
+FLAG_BF16 = 0x10
 
 OK = 0
 WARN_OVERFLOW = 1

@@ -76,6 +76,10 @@ struct knng_ctx {
     uint64_t *keys = nullptr, *keys2 = nullptr;
     int *locks = nullptr, *ibuf = nullptr, *cand = nullptr, *err = nullptr, *pcursor = nullptr;
     int *pchunk = nullptr, *pool_next = nullptr;
+    uint16_t *Xb = nullptr, *Xb2 = nullptr;
+    float *xnorm = nullptr, *xnorm2 = nullptr;
+    int dpb = 0;
+    bool bf16 = false;
     uint64_t *pbucket = nullptr, *ppool = nullptr;
     int32_t *sigma = nullptr, *sigma_inv = nullptr, *total_perm = nullptr, *total_inv = nullptr;
     long long *stats = nullptr, *it_stats = nullptr;
@@ -86,6 +90,8 @@ struct knng_ctx {
     DevState dev(bool gate) const {
         DevState st;
         st.X = X;
+        st.Xb = Xb;
+        st.xnorm = xnorm;
         st.keys = keys;
         st.locks = locks;
         st.pcursor = pcursor;
@@ -105,7 +111,10 @@ struct knng_ctx {
         st.stats = stats;
         st.it_stats = it_stats;
         st.n = n;
+        st.d = d;
         st.dp = dp;
+        st.dpb = dpb;
+        st.bf16 = bf16 ? 1 : 0;
         st.nv = nv;
         st.K = K;
         st.s = s;
@@ -142,6 +151,8 @@ int ctx_alloc(knng_ctx *c) {
     const size_t oS = take(sizeof(long long) * kStatCount);
     const size_t oT = take(sizeof(long long) * kItCount * kMaxLocalIters);
     const size_t oE = take(sizeof(int));
+    const size_t oXb = c->bf16 ? take(sizeof(uint16_t) * n * c->dpb) : 0;
+    const size_t oXn = c->bf16 ? take(sizeof(float) * n) : 0;
     cudaError_t e = cudaMallocAsync((void **)&c->arena, off, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -170,6 +181,10 @@ int ctx_alloc(knng_ctx *c) {
     c->stats = (long long *)(a + oS);
     c->it_stats = (long long *)(a + oT);
     c->err = (int *)(a + oE);
+    if (c->bf16) {
+        c->Xb = (uint16_t *)(a + oXb);
+        c->xnorm = (float *)(a + oXn);
+    }
     KNNG_TRY(cudaMemsetAsync(c->locks, 0, sizeof(int) * nint, c->stream));
     KNNG_TRY(cudaMemsetAsync(c->ibuf, 0, sizeof(int) * 6 * n, c->stream));
     KNNG_TRY(cudaMemsetAsync(c->stats, 0, sizeof(long long) * kStatCount, c->stream));
@@ -190,6 +205,10 @@ int ctx_stage(knng_ctx *c, const float *data) {
     }
     KNNG_TRY(launch_stage(src, c->n, c->d, c->X, c->dp, c->stream));
     c->launches++;
+    if (c->bf16) {
+        KNNG_TRY(launch_stage_bf16(c->X, c->n, c->dp, c->d, c->Xb, c->dpb, c->xnorm, c->stream));
+        c->launches++;
+    }
     if (tmp) KNNG_TRY(cudaFreeAsync(tmp, c->stream));
     return KNNG_OK;
 }
@@ -221,6 +240,9 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
     c->delta = delta;
     c->seed = seed;
     c->flags = flags;
+    // bf16 tensor-core dots where the contraction is long enough to pay
+    c->bf16 = (flags & KNNG_FLAG_BF16) && d >= 64;
+    c->dpb = (d + 63) & ~63;
     c->stream = (cudaStream_t)stream;
     c->thr = (double)delta * (double)n * (double)K;
     rc = ctx_alloc(c);
@@ -262,6 +284,10 @@ int enqueue_reorder(knng_ctx *c) {
     c->launches += 2;
     std::swap(c->X, c->X2);
     std::swap(c->keys, c->keys2);
+    if (c->bf16) {
+        KNNG_TRY(launch_stage_bf16(c->X, c->n, c->dp, c->d, c->Xb, c->dpb, c->xnorm, c->stream));
+        c->launches++;
+    }
     c->reordered = true;
     return KNNG_OK;
 }

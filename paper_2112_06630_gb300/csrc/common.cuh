@@ -168,6 +168,8 @@ enum ItStat : int {
 
 struct DevState {
     const float *X;      // n x dp, zero padded
+    const uint16_t *Xb;  // n x dpb bf16 bits (zero padded to a multiple of 64), bf16 mode only
+    const float *xnorm;  // n squared norms of the bf16 rows, bf16 mode only
     uint64_t *keys;      // n x K, ascending
     int *locks;          // n, taken only when a proposal bucket is full
     int *pcursor;        // n, proposals reserved in each node's bucket this iteration
@@ -183,7 +185,8 @@ struct DevState {
     long long *stats;
     long long *it_stats;       // (max_iters + 2) x kItCount
     int64_t n;
-    int dp, nv, K, s, R, cap;
+    int d, dp, nv, K, s, R, cap, dpb;
+    int bf16;                  // 1: high-d joins use bf16 tensor-core Gram blocks
     double thr;                // delta * n * K
 };
 

@@ -20,6 +20,9 @@ cudaError_t launch_count(const DevState &st, int li, cudaStream_t s);
 cudaError_t launch_sample(const DevState &st, int li, int it, uint64_t seed, cudaStream_t s);
 cudaError_t launch_join(const DevState &st, int li, cudaStream_t s);
 cudaError_t launch_merge(const DevState &st, int li, cudaStream_t s);
+cudaError_t launch_tile_join(const DevState &st, int li, bool bf16, cudaStream_t s);
+cudaError_t launch_stage_bf16(const float *X, int64_t n, int dp, int d, uint16_t *Xb, int dpb, float *nrm,
+                              cudaStream_t s);
 cudaError_t launch_greedy_reorder(const uint64_t *keys, int64_t n, int K, int reading_b, int32_t *sigma,
                                   int32_t *sigma_inv, cudaStream_t s);
 cudaError_t launch_permute(const DevState &src, float *X_dst, uint64_t *keys_dst, const int32_t *sigma,

@@ -30,17 +30,14 @@
 // Since every float32 distance in the library uses the same arithmetic, a pair
 // always yields the same key, and each list ends as the K smallest distinct
 // keys of its start entries and all proposals it received, whatever the order.
-#include "internal.h"
+#include "join_common.cuh"
 
 namespace knng {
 
 namespace {
-constexpr int kSetMax = 64;
-constexpr int kHashBits = 8;  // 256-slot hash set for repeat removal (at most 2 * (32 + 72) ids)
 constexpr int kJoinWarps = 4;
 constexpr int kMergeWarps = 8;
-constexpr int kLockSpins = 1 << 20;
-constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kTileMinNv = 16;  // rows longer than 64 floats go to the tile kernel
 
 struct JoinLayout {
     int raw_max;      // ints for raw candidate ids
@@ -66,31 +63,6 @@ __host__ __device__ inline JoinLayout join_layout(int cap, int nv, bool rows_sme
     return L;
 }
 
-// q / divisor for q < 2^12 and 2 <= divisor <= 64 given magic = ceil(2^32 /
-// divisor): exact, the rounding error stays below 2^-20.  Divisor 1 (magic
-// would need 33 bits) is passed through.
-__device__ __forceinline__ uint32_t div_small(uint32_t q, uint32_t divisor, uint32_t magic) {
-    return divisor == 1u ? q : __umulhi(q, magic);
-}
-__device__ __forceinline__ uint32_t div_magic(uint32_t divisor) {
-    return divisor > 1u ? (uint32_t)((0x100000000ull + divisor - 1) / divisor) : 0u;
-}
-
-// Insert x into the list held one entry per lane (Lk, lane k = entry k of K,
-// ascending): only if it orders before the worst entry and its id is not
-// listed.  Warp-uniform result: true if inserted.
-__device__ __forceinline__ bool warp_insert(uint64_t &Lk, uint64_t x, int K) {
-    const unsigned lane = lane_id();
-    const bool valid = (int)lane < K;
-    const uint64_t worst = __shfl_sync(kFull, Lk, K - 1);
-    if (x >= worst) return false;
-    if (__ballot_sync(kFull, valid && key_id(Lk) == key_id(x))) return false;
-    const unsigned gt = __ballot_sync(kFull, valid && Lk > x);
-    const int pos = __ffs(gt) - 1;  // first entry ordered after x
-    const uint64_t up = __shfl_up_sync(kFull, Lk, 1);
-    if (valid && (int)lane >= pos) Lk = (int)lane == pos ? x : up;
-    return true;
-}
 }  // namespace
 
 template <bool kRowsSmem>
@@ -105,7 +77,7 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
 
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
-    const int K = st.K, R = st.R, cap = st.cap, nv = st.nv;
+    const int K = st.K, cap = st.cap, nv = st.nv;
     const JoinLayout lay = join_layout(cap, nv, kRowsSmem);
     unsigned char *wbase = smem + (size_t)warp * lay.per_warp;
     int *sid = reinterpret_cast<int *>(wbase);
@@ -125,65 +97,9 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long u = gw; u < st.n; u += nw) {
         // ---- 1. candidates of u, repeats removed (new first, then old)
-        const size_t cb = (size_t)u * cap;
-        const int fn = st.fwd_new[u], fo = st.fwd_old[u];
-        const int rn = min(st.fill_new[u], R), ro = min(st.fill_old[u], R);
-        __syncwarp();
-        if (lane == 0) {  // reverse degrees of the next iteration start from zero
-            st.rev_new[u] = 0;
-            st.rev_old[u] = 0;
-        }
-        const int nnew_raw = fn + rn;
-        const int total = nnew_raw + fo + ro;
-        w_candids += total;
-        if (nnew_raw == 0) continue;  // no new candidate: no join pair
-        for (int idx = lane; idx < total; idx += 32) {
-            int v;
-            if (idx < fn) v = st.cand_new[cb + idx];
-            else if (idx < nnew_raw) v = st.cand_new[cb + K + (idx - fn)];
-            else if (idx < nnew_raw + fo) v = st.cand_old[cb + (idx - nnew_raw)];
-            else v = st.cand_old[cb + K + (idx - nnew_raw - fo)];
-            raw[idx] = v;
-        }
-        __syncwarp();
-        for (int i = lane; i < (1 << kHashBits); i += 32) hset[i] = -1;
-        __syncwarp();
-        // repeats removed with a shared-memory hash set: new entries first, so
-        // an id that is both new and old stays new; of repeats of one kind the
-        // copy whose insertion wins stays (the set does not depend on which)
-        int ns = 0, m = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            const int lo_i = pass ? nnew_raw : 0, hi_i = pass ? total : nnew_raw;
-            for (int b0 = lo_i; b0 < hi_i; b0 += 32) {
-                const int idx = b0 + lane;
-                bool keep = false;
-                int v = -1;
-                if (idx < hi_i) {
-                    v = raw[idx];
-                    unsigned h = ((unsigned)v * 0x9E3779B1u) >> (32 - kHashBits);
-                    for (int probe = 0; probe < (1 << kHashBits); ++probe) {
-                        const int prev = atomicCAS(hset + h, -1, v);
-                        if (prev == -1) {
-                            keep = true;
-                            break;
-                        }
-                        if (prev == v) break;
-                        h = (h + 1) & ((1u << kHashBits) - 1);
-                    }
-                }
-                const unsigned km = __ballot_sync(kFull, keep);
-                const int pos = ns + __popc(km & lanemask_lt());
-                if (keep && pos < kSetMax) sid[pos] = v;
-                if (!pass) m += __popc(km);
-                ns += __popc(km);
-            }
-            __syncwarp();
-        }
-        if (ns > kSetMax) {
-            w_setovf += ns - kSetMax;
-            ns = kSetMax;
-        }
-        m = min(m, ns);
+        int ns, m;
+        w_candids += warp_gather_candidates(st, u, raw, hset, sid, ns, m, w_setovf);
+        if (ns == 0) continue;  // no new candidate: no join pair
         const int o = ns - m;
         __syncwarp();
         // ---- 2. snapshot worst keys, clear masks, stage rows
@@ -269,22 +185,6 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
             unsigned long long rest = mask[t];
             for (int r = 0; r < base[t]; ++r) rest &= rest - 1;
             w_ovf += __popcll(rest);
-            bool got = false;
-            if (lane == 0) {
-                for (int spin = 0; spin < kLockSpins; ++spin) {
-                    if (atomicCAS(st.locks + p, 0, 1) == 0) {
-                        got = true;
-                        break;
-                    }
-                    __nanosleep(spin < 64 ? 64 : 512);
-                }
-                if (got) __threadfence();
-            }
-            got = __shfl_sync(kFull, got, 0);
-            if (!got) {
-                ++w_to;
-                continue;
-            }
             const float4 *rt = kRowsSmem ? rows + t * rs : X4 + (size_t)p * nv;
             uint64_t xs[2];
 #pragma unroll
@@ -296,17 +196,9 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
                     xs[h] = make_key(l2sq_rows(rt, rj, nv), (uint32_t)sid[j], kFlagNew | kFlagIns);
                 }
             }
-            uint64_t *row = st.keys + (size_t)p * K;
-            uint64_t Lk = (int)lane < K ? __ldcg(row + lane) : kKeyEmpty;
-            for (unsigned long long mm = rest; mm; mm &= mm - 1) {
-                const int j = __ffsll((long long)mm) - 1;
-                const uint64_t xa = __shfl_sync(kFull, xs[0], j & 31), xb = __shfl_sync(kFull, xs[1], j & 31);
-                w_ins += warp_insert(Lk, j < 32 ? xa : xb, K);
-            }
-            if ((int)lane < K) __stcg(row + lane, Lk);
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) atomicExch(st.locks + p, 0);
+            const int ins = warp_locked_insert(st, p, rest, xs[0], xs[1]);
+            if (ins < 0) ++w_to;
+            else w_ins += ins;
         }
         __syncwarp();
     }
@@ -439,6 +331,9 @@ cudaError_t launch_join_t(const DevState &st, int li, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_join(const DevState &st, int li, cudaStream_t s) {
+    // high dimensions: block-per-node tiles (bf16 tensor cores when asked)
+    if (st.bf16) return launch_tile_join(st, li, true, s);
+    if (st.nv > kTileMinNv) return launch_tile_join(st, li, false, s);
     const JoinLayout lay = join_layout(st.cap, st.nv, true);
     if (lay.per_warp * kJoinWarps <= 110 * 1024) return launch_join_t<true>(st, li, s);
     return launch_join_t<false>(st, li, s);

@@ -1,0 +1,150 @@
+// join_common.cuh -- pieces shared by the two local-join kernels (the
+// warp-per-node kernel for low dimensions and the block-per-node tile kernel
+// for high dimensions) and the list-merge kernel.
+#pragma once
+
+#include "internal.h"
+
+namespace knng {
+
+constexpr int kSetMax = 64;      // candidates per node and iteration after repeats are removed
+constexpr int kHashBits = 8;     // 256-slot hash set for repeat removal (at most 2 * (32 + 72) ids)
+constexpr int kLockSpins = 1 << 20;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// q / divisor for q < 2^12 and 2 <= divisor <= 64 given magic = ceil(2^32 /
+// divisor): exact, the rounding error stays below 2^-20.  Divisor 1 (magic
+// would need 33 bits) is passed through.
+__device__ __forceinline__ uint32_t div_small(uint32_t q, uint32_t divisor, uint32_t magic) {
+    return divisor == 1u ? q : __umulhi(q, magic);
+}
+__device__ __forceinline__ uint32_t div_magic(uint32_t divisor) {
+    return divisor > 1u ? (uint32_t)((0x100000000ull + divisor - 1) / divisor) : 0u;
+}
+
+// Insert x into the list held one entry per lane (Lk, lane k = entry k of K,
+// ascending): only if it orders before the worst entry and its id is not
+// listed.  Warp-uniform result: true if inserted.
+__device__ __forceinline__ bool warp_insert(uint64_t &Lk, uint64_t x, int K) {
+    const unsigned lane = lane_id();
+    const bool valid = (int)lane < K;
+    const uint64_t worst = __shfl_sync(kFull, Lk, K - 1);
+    if (x >= worst) return false;
+    if (__ballot_sync(kFull, valid && key_id(Lk) == key_id(x))) return false;
+    const unsigned gt = __ballot_sync(kFull, valid && Lk > x);
+    const int pos = __ffs(gt) - 1;  // first entry ordered after x
+    const uint64_t up = __shfl_up_sync(kFull, Lk, 1);
+    if (valid && (int)lane >= pos) Lk = (int)lane == pos ? x : up;
+    return true;
+}
+
+// Node u's sampled candidates (one warp): the forward part written by u's
+// sampling warp and the reverse part filled by other warps, repeats removed
+// with a shared-memory hash set (new entries first, so an id that is both new
+// and old stays new; of repeats of one kind the copy whose insertion wins
+// stays, the set does not depend on which).  Writes sid[0 .. ns), new ones
+// first (m of them), capped at kSetMax.  raw must hold 2 * cap ints and hset
+// 2^kHashBits ints.  Lane 0 also restarts u's reverse degrees for the next
+// iteration.  Returns total raw ids read; ns = 0 when u has no new candidate
+// (no join pair).  Results are warp-uniform.
+__device__ __forceinline__ int warp_gather_candidates(const DevState &st, long long u, int *raw, int *hset, int *sid,
+                                                      int &ns_out, int &m_out, long long &setovf) {
+    const unsigned lane = lane_id();
+    const int K = st.K, R = st.R;
+    const size_t cb = (size_t)u * st.cap;
+    const int fn = st.fwd_new[u], fo = st.fwd_old[u];
+    const int rn = min(st.fill_new[u], R), ro = min(st.fill_old[u], R);
+    __syncwarp();
+    if (lane == 0) {
+        st.rev_new[u] = 0;
+        st.rev_old[u] = 0;
+    }
+    const int nnew_raw = fn + rn;
+    const int total = nnew_raw + fo + ro;
+    ns_out = 0;
+    m_out = 0;
+    if (nnew_raw == 0) return total;
+    for (int idx = lane; idx < total; idx += 32) {
+        int v;
+        if (idx < fn) v = st.cand_new[cb + idx];
+        else if (idx < nnew_raw) v = st.cand_new[cb + K + (idx - fn)];
+        else if (idx < nnew_raw + fo) v = st.cand_old[cb + (idx - nnew_raw)];
+        else v = st.cand_old[cb + K + (idx - nnew_raw - fo)];
+        raw[idx] = v;
+    }
+    for (int i = lane; i < (1 << kHashBits); i += 32) hset[i] = -1;
+    __syncwarp();
+    int ns = 0, m = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int lo_i = pass ? nnew_raw : 0, hi_i = pass ? total : nnew_raw;
+        for (int b0 = lo_i; b0 < hi_i; b0 += 32) {
+            const int idx = b0 + lane;
+            bool keep = false;
+            int v = -1;
+            if (idx < hi_i) {
+                v = raw[idx];
+                unsigned h = ((unsigned)v * 0x9E3779B1u) >> (32 - kHashBits);
+                for (int probe = 0; probe < (1 << kHashBits); ++probe) {
+                    const int prev = atomicCAS(hset + h, -1, v);
+                    if (prev == -1) {
+                        keep = true;
+                        break;
+                    }
+                    if (prev == v) break;
+                    h = (h + 1) & ((1u << kHashBits) - 1);
+                }
+            }
+            const unsigned km = __ballot_sync(kFull, keep);
+            const int pos = ns + __popc(km & lanemask_lt());
+            if (keep && pos < kSetMax) sid[pos] = v;
+            if (!pass) m += __popc(km);
+            ns += __popc(km);
+        }
+        __syncwarp();
+    }
+    if (ns > kSetMax) {
+        setovf += ns - kSetMax;
+        ns = kSetMax;
+    }
+    ns_out = ns;
+    m_out = min(m, ns);
+    return total;
+}
+
+// Locked insertion (one warp) of proposals into node p's list, used when a
+// proposal bucket is full.  Lane j holds the key of partner j in x0 and of
+// partner 32 + j in x1; `rest` selects the partners.  The lock wait is
+// bounded; returns -1 when it gave up, else the number of insertions.
+__device__ __forceinline__ int warp_locked_insert(const DevState &st, uint32_t p, unsigned long long rest,
+                                                  uint64_t x0, uint64_t x1) {
+    const unsigned lane = lane_id();
+    const int K = st.K;
+    bool got = false;
+    if (lane == 0) {
+        for (int spin = 0; spin < kLockSpins; ++spin) {
+            if (atomicCAS(st.locks + p, 0, 1) == 0) {
+                got = true;
+                break;
+            }
+            __nanosleep(spin < 64 ? 64 : 512);
+        }
+        if (got) __threadfence();
+    }
+    got = __shfl_sync(kFull, got, 0);
+    if (!got) return -1;
+    uint64_t *row = st.keys + (size_t)p * K;
+    uint64_t Lk = (int)lane < K ? __ldcg(row + lane) : kKeyEmpty;
+    int ins = 0;
+    for (unsigned long long mm = rest; mm; mm &= mm - 1) {
+        const int j = __ffsll((long long)mm) - 1;
+        const uint64_t xa = __shfl_sync(kFull, x0, j & 31), xb = __shfl_sync(kFull, x1, j & 31);
+        ins += warp_insert(Lk, j < 32 ? xa : xb, K);
+    }
+    if ((int)lane < K) __stcg(row + lane, Lk);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicExch(st.locks + p, 0);
+    return ins;
+}
+
+}  // namespace knng

@@ -102,7 +102,9 @@ CASES = [
     (1800, 3, 16, 0.5, 6),
     (1200, 17, 32, 0.3, 5),
     (900, 40, 8, 0.5, 4),
-    (400, 600, 12, 0.5, 3),
+    (400, 600, 12, 0.5, 3),     # block-per-node tile kernel (rows > 64 floats)
+    (700, 65, 32, 0.3, 4),      # tile kernel, ragged last 64-float chunk
+    (1500, 100, 20, 0.5, 3),    # tile kernel, two passes of new rows possible
 ]
 
 
@@ -150,6 +152,41 @@ def test_bucket_overflow_paths_match_oracle_bit_exact(pool, monkeypatch):
     oi, od, of = st.state()
     assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
     assert ch == r["changes"]
+
+
+@pytest.mark.parametrize("n,d,K,rho", [(1200, 64, 16, 0.5), (800, 150, 20, 1.0), (600, 128, 32, 0.3)])
+def test_bf16_tensor_core_join_exact_on_small_integers(n, d, K, rho):
+    """bf16 tensor-core Gram blocks: with integer data in [0, 3] every product
+    and every partial sum is an exact float32 integer, so the expansion
+    |x|^2 + |y|^2 - 2 x.y equals the difference form and the iteration must
+    match the oracle bit for bit."""
+    x = _int_data(n, d, 4, seed=d)
+    ids0, new0 = workloads.random_graph(n, K, seed=n + 3, p_new=0.6)
+    with knng.Context(_cuda(x), K, rho=rho, seed=5, graph=(ids0, new0), iter=0, flags=knng.FLAG_BF16) as c:
+        conv, ch = c.iterate()
+        gi, gd, gf = c.state()
+        assert c.stats()["set_overflow"] == 0
+    st = oracle.State(x, K, rho, seed=5)
+    st.init_graph(ids0, new0, 0)
+    r = st.iterate()
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    assert ch == r["changes"]
+
+
+def test_bf16_build_recall_and_rerank_on_mnist_shaped_data():
+    """bf16 dots with float32 re-rank on MNIST-shaped integer data (0..255,
+    mostly zeros): recall within 0.005 of the float32 build, and every
+    returned distance the float32 difference form (1e-4 of float64)."""
+    x = workloads.mnist_like(6000, 784, seed=1)
+    rows = np.random.default_rng(2).choice(len(x), 400, replace=False)
+    ei, _ = oracle.bruteforce(x, 20, rows)
+    fi, fd, _ = knng.knng_build(_cuda(x), 20, 0.5, 0.001, 15, seed=0)
+    bi, bd, st = knng.knng_build(_cuda(x), 20, 0.5, 0.001, 15, seed=0, flags=knng.FLAG_BF16)
+    bi, bd = bi.cpu().numpy(), bd.cpu().numpy()
+    assert metrics.check_graph(x, bi, bd, rows=rows) == []
+    rf, rb = metrics.recall(x, fi.cpu().numpy(), ei, rows), metrics.recall(x, bi, ei, rows)
+    assert rb >= rf - 0.005, (rb, rf)
 
 
 def test_several_iterations_match_oracle_bit_exact():
