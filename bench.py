@@ -148,12 +148,14 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
 
-    w, x = workloads.make(WORKLOAD)
+    w, x = workloads.make(args.workload)
     xd = torch.from_numpy(x).to(device)
     stream = torch.cuda.current_stream(device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
-    flags = knng.FLAG_REORDER if args.reorder else 0
+    flags = (knng.FLAG_REORDER if args.reorder else 0) | (knng.FLAG_BF16 if args.bf16 else 0)
     dp = (w.d + 3) // 4 * 4
+    if args.bf16 and w.d >= 64:
+        dp = (w.d + 63) // 64 * 64 // 2  # bf16 rows: half the bytes of float32
 
     def build(tflags=0):
         return knng.knng_build(xd, w.K, w.rho, w.delta, w.max_iters, seed=0, flags=flags | tflags)
@@ -235,9 +237,10 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": round(value, 6), "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 4), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
-                   "max_iters": w.max_iters, "reorder": bool(args.reorder), "parallelism": f"replicas{ws}",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if args.bf16 else "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
+                   "max_iters": w.max_iters, "reorder": bool(args.reorder), "bf16": bool(args.bf16),
+                   "parallelism": f"replicas{ws}",
                    "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
         "recall_at_k": round(rec, 5), "recall_rows": RECALL_ROWS,
         "iterations": stats["iterations"], "dist_evals": stats["dist_evals"],
@@ -273,7 +276,7 @@ def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    w, x = workloads.make(WORKLOAD)
+    w, x = workloads.make(args.workload)
     import oracle
     oracle._load()
     for _ in range(args.warmup):
@@ -285,7 +288,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 2),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
+        "config": {"workload": args.workload, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
                    "max_iters": w.max_iters, "parallelism": "cpu1"},
         "cpu_baseline": {"value": round(v, 4), "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"whole workload ({w.n} points) per step, single thread"},
@@ -301,6 +304,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--reorder", action="store_true", help="Algorithm 1 relabelling after iteration 1")
+    ap.add_argument("--bf16", action="store_true", help="bf16 tensor-core dots for d >= 64, float32 re-rank")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS),
+                    help="another workload than the headline one (measurement table)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":

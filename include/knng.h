@@ -181,6 +181,31 @@ int knng_get_stats(knng_ctx *ctx, knng_stats *stats);
 /* Free a context and its device memory (stream-ordered).  NULL is fine. */
 int knng_destroy(knng_ctx *ctx);
 
+/* One data set of a batched build: n x d float32 points (host or device),
+ * outputs n x K (host or device), ids local to the data set. */
+typedef struct knng_desc {
+    const float *data;
+    int64_t n;
+    int32_t d;
+    int32_t *ids;
+    float *dists;
+} knng_desc;
+
+/*
+ * K-NNGs of many independent data sets in one run (each as knng_build with
+ * the same K, rho, delta, max_iters, seed and flags): the data sets share one
+ * node space, so every step of every iteration is one kernel launch for all
+ * of them.  Data sets of different d are zero-padded to the widest (this
+ * leaves every distance unchanged); each stops on its own change count
+ * (delta * n_b * K), and the random streams are keyed by ids local to the data
+ * set, so each result equals what knng_build_ex gives for that data set alone.
+ * Requires 2 <= n_b, K <= n_b - 1 for every data set and a total below 2^30
+ * nodes; KNNG_FLAG_REORDER is not supported here (KNNG_ERR_UNSUPPORTED).
+ * Returns when all outputs are written.
+ */
+int knng_build_batched(const knng_desc *descs, int count, int K, float rho, float delta, int max_iters,
+                       uint64_t seed, uint32_t flags, void *stream, knng_stats *stats);
+
 /*
  * Exact K-NNG by brute force (Section 2: every distance, the K smallest per
  * point by (dist, id), float32 difference-form distances).  rows (host or

@@ -17,7 +17,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "KnngError", "Stats", "Context", "knng_build", "knng_bruteforce", "lib_path",
+    "KnngError", "Stats", "Context", "knng_build", "knng_build_batched", "knng_bruteforce", "lib_path", "Desc",
     "FLAG_REORDER", "FLAG_REORDER_B", "FLAG_TIMING", "FLAG_GRAPH", "FLAG_BF16", "version", "strerror", "load",
 ]
 
@@ -53,6 +53,11 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class Desc(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32),
+                ("ids", ctypes.c_void_p), ("dists", ctypes.c_void_p)]
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -81,6 +86,7 @@ def _load():
         "knng_get_stats": (i32, [P, P]),
         "knng_destroy": (i32, [P]),
         "knng_bruteforce": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
+        "knng_build_batched": (i32, [P, i32, i32, f32, f32, i32, u64, u32, P, P]),
         "knng_strerror": (ctypes.c_char_p, [i32]),
         "knng_version": (ctypes.c_char_p, []),
     }
@@ -192,6 +198,30 @@ def knng_build(data, K: int, rho: float = 1.0, delta: float = 0.001, max_iters: 
     info = st.as_dict()
     info["overflow_warning"] = rc == WARN_OVERFLOW
     return ids, dists, info
+
+
+def knng_build_batched(datasets, K: int, rho: float = 1.0, delta: float = 0.001, max_iters: int = 10,
+                       seed: int = 0, flags: int = 0, stream=None):
+    """K-NNGs of many independent data sets in one run (one launch per step
+    for all of them).  `datasets`: sequence of (n_b, d_b) float32 arrays or
+    CUDA tensors.  Returns ([(ids, dists) per data set], stats_dict)."""
+    keep, outs = [], []
+    descs = (Desc * len(datasets))()
+    dev_any = False
+    for b, data in enumerate(datasets):
+        ptr, k, n, d, dev = _as_input(data)
+        dev_any = dev_any or dev
+        ids, dists, ip, dp = _outputs(n, K, dev, k if dev else None)
+        keep.append(k)
+        outs.append((ids, dists))
+        descs[b] = Desc(ptr, n, d, ip, dp)
+    st = Stats()
+    rc = _lib.knng_build_batched(ctypes.addressof(descs), len(datasets), K, rho, delta, max_iters, seed, flags,
+                                 _stream_ptr(stream, dev_any), ctypes.byref(st))
+    _check(rc, "knng_build_batched")
+    info = st.as_dict()
+    info["overflow_warning"] = rc == WARN_OVERFLOW
+    return outs, info
 
 
 def knng_bruteforce(data, K: int, rows=None, stream=None):

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -16,7 +17,6 @@ using namespace knng;
 
 namespace {
 
-constexpr int kMaxLocalIters = 1024;
 constexpr int kMaxItersArg = 1000;
 
 int rev_capacity(int s) { return 2 * s + 8; }
@@ -84,6 +84,13 @@ struct knng_ctx {
     int32_t *sigma = nullptr, *sigma_inv = nullptr, *total_perm = nullptr, *total_inv = nullptr;
     long long *stats = nullptr, *it_stats = nullptr;
 
+    // batched mode
+    int nds = 0;
+    unsigned char *barena = nullptr;
+    int *ds = nullptr, *ds_n = nullptr;
+    long long *ds_off = nullptr, *ds_changes = nullptr;
+    double *ds_thr = nullptr;
+
     std::vector<cudaEvent_t> ev;  // start/stop pairs around join launches
     std::vector<int> ev_li;       // iteration index of each pair
 
@@ -121,6 +128,11 @@ struct knng_ctx {
         st.R = R;
         st.cap = cap;
         st.thr = gate ? thr : -1.0;
+        st.ds = ds;
+        st.ds_off = ds_off;
+        st.ds_n = ds_n;
+        st.ds_thr = ds_thr;
+        st.ds_changes = ds_changes;
         return st;
     }
 };
@@ -213,11 +225,11 @@ int ctx_stage(knng_ctx *c, const float *data) {
     return KNNG_OK;
 }
 
+// data == nullptr: allocate only (the batched build stages its data sets)
 int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float rho, float delta, uint64_t seed,
                uint32_t flags, void *stream) {
     if (!out) return KNNG_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!data) return KNNG_ERR_INVALID_ARG;
     int rc = check_args(n, d, K, rho, delta);
     if (rc) return rc;
     knng_ctx *c = new (std::nothrow) knng_ctx();
@@ -246,7 +258,7 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
     c->stream = (cudaStream_t)stream;
     c->thr = (double)delta * (double)n * (double)K;
     rc = ctx_alloc(c);
-    if (!rc) rc = ctx_stage(c, data);
+    if (!rc && data) rc = ctx_stage(c, data);
     if (!rc && c->total_perm) {
         // the relabelling original -> spot starts as the identity
         rc = cuda_code(launch_iota(c->total_perm, c->n, c->stream));
@@ -344,6 +356,10 @@ const char *knng_version(void) { return "knng-gb300 0.1 (sm_103a)"; }
 
 int knng_init(knng_ctx **out, const float *data, int64_t n, int d, int K, float rho, float delta, uint64_t seed,
               uint32_t flags, void *stream) {
+    if (!data) {
+        if (out) *out = nullptr;
+        return KNNG_ERR_INVALID_ARG;
+    }
     int rc = ctx_create(out, data, n, d, K, rho, delta, seed, flags, stream);
     if (rc) return rc;
     knng_ctx *c = *out;
@@ -361,7 +377,7 @@ int knng_init(knng_ctx **out, const float *data, int64_t n, int d, int K, float 
 int knng_init_from_graph(knng_ctx **out, const float *data, int64_t n, int d, int K, float rho, float delta,
                          uint64_t seed, uint32_t flags, void *stream, const int32_t *ids, const uint8_t *is_new,
                          int iter) {
-    if (!ids || !is_new || iter < 0) return KNNG_ERR_INVALID_ARG;
+    if (!data || !ids || !is_new || iter < 0) return KNNG_ERR_INVALID_ARG;
     int rc = ctx_create(out, data, n, d, K, rho, delta, seed, flags, stream);
     if (rc) return rc;
     knng_ctx *c = *out;
@@ -572,6 +588,7 @@ int knng_destroy(knng_ctx *c) {
     if (!c) return KNNG_OK;
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->arena) cudaFreeAsync(c->arena, c->stream);
+    if (c->barena) cudaFreeAsync(c->barena, c->stream);
     delete c;
     return KNNG_OK;
 }
@@ -599,6 +616,107 @@ int knng_build_ex(const float *data, int64_t n, int d, int K, float rho, float d
 int knng_build(const float *data, int64_t n, int d, int K, float rho, float delta, int max_iters, uint64_t seed,
                int32_t *ids, float *dists) {
     return knng_build_ex(data, n, d, K, rho, delta, max_iters, seed, 0u, nullptr, ids, dists, nullptr);
+}
+
+int knng_build_batched(const knng_desc *descs, int count, int K, float rho, float delta, int max_iters,
+                       uint64_t seed, uint32_t flags, void *stream, knng_stats *stats) {
+    if (!descs || count < 1 || max_iters < 0 || max_iters > kMaxItersArg) return KNNG_ERR_INVALID_ARG;
+    if (flags & (KNNG_FLAG_REORDER | KNNG_FLAG_REORDER_B)) return KNNG_ERR_UNSUPPORTED;
+    int64_t ntot = 0;
+    int dmax = 0;
+    std::vector<long long> off(count + 1);
+    std::vector<int> nn(count);
+    std::vector<double> thr(count);
+    for (int b = 0; b < count; ++b) {
+        const knng_desc &e = descs[b];
+        if (!e.data || !e.ids || !e.dists || e.n < 2 || e.d < 1 || K > e.n - 1) return KNNG_ERR_INVALID_ARG;
+        off[b] = ntot;
+        nn[b] = (int)e.n;
+        thr[b] = (double)delta * (double)e.n * (double)K;
+        ntot += e.n;
+        dmax = std::max(dmax, e.d);
+    }
+    off[count] = ntot;
+    knng_ctx *c = nullptr;
+    int rc = ctx_create(&c, nullptr, ntot, dmax, K, rho, delta, seed, flags, stream);
+    if (rc) return rc;
+    c->thr = -1.0;  // convergence is decided per data set
+    c->nds = count;
+    cudaStream_t s = c->stream;
+    cudaError_t e = cudaSuccess;
+    // per-data-set arrays
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o += align256(bytes);
+        return r;
+    };
+    const size_t oDs = take(sizeof(int) * ntot), oOff = take(sizeof(long long) * (count + 1)),
+                 oN = take(sizeof(int) * count), oT = take(sizeof(double) * count),
+                 oC = take(sizeof(long long) * (size_t)count * kMaxLocalIters);
+    e = cudaMallocAsync((void **)&c->barena, o, s);
+    if (e == cudaSuccess) {
+        c->ds = (int *)(c->barena + oDs);
+        c->ds_off = (long long *)(c->barena + oOff);
+        c->ds_n = (int *)(c->barena + oN);
+        c->ds_thr = (double *)(c->barena + oT);
+        c->ds_changes = (long long *)(c->barena + oC);
+        e = cudaMemcpyAsync(c->ds_off, off.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ds_n, nn.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ds_thr, thr.data(), sizeof(double) * count, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->ds_changes, 0, sizeof(long long) * (size_t)count * kMaxLocalIters, s);
+    if (e == cudaSuccess) e = launch_ds_map(c->ds_off, count, ntot, c->ds, s);
+    // stage every data set into its node range (zero padding to the widest row
+    // leaves every distance unchanged)
+    for (int b = 0; e == cudaSuccess && b < count; ++b) {
+        const knng_desc &d = descs[b];
+        const float *src = d.data;
+        float *tmp = nullptr;
+        if (!is_device_ptr(d.data)) {
+            e = cudaMallocAsync((void **)&tmp, sizeof(float) * d.n * d.d, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, d.data, sizeof(float) * d.n * d.d, cudaMemcpyHostToDevice, s);
+            src = tmp;
+        }
+        if (e == cudaSuccess) e = launch_stage(src, d.n, d.d, c->X + (size_t)off[b] * c->dp, c->dp, s);
+        if (tmp) cudaFreeAsync(tmp, s);
+    }
+    if (e == cudaSuccess && c->bf16) e = launch_stage_bf16(c->X, ntot, c->dp, dmax, c->Xb, c->dpb, c->xnorm, s);
+    if (e == cudaSuccess) e = launch_init_random(c->dev(false), seed, c->err, s);
+    c->launches += count + 3;
+    if (e != cudaSuccess) {
+        knng_destroy(c);
+        return cuda_code(e);
+    }
+    rc = knng_run(c, max_iters);
+    // output into one concatenated buffer, then one copy per data set
+    int32_t *oi = nullptr;
+    float *od = nullptr;
+    if (!rc) {
+        e = cudaMallocAsync((void **)&oi, sizeof(int32_t) * ntot * K, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&od, sizeof(float) * ntot * K, s);
+        if (e == cudaSuccess) e = launch_output(c->dev(false), nullptr, nullptr, oi, od, s);
+        c->launches++;
+        for (int b = 0; e == cudaSuccess && b < count; ++b) {
+            e = cudaMemcpyAsync(descs[b].ids, oi + off[b] * K, sizeof(int32_t) * descs[b].n * K, cudaMemcpyDefault, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(descs[b].dists, od + off[b] * K, sizeof(float) * descs[b].n * K, cudaMemcpyDefault, s);
+        }
+        if (oi) cudaFreeAsync(oi, s);
+        if (od) cudaFreeAsync(od, s);
+        if (e != cudaSuccess) rc = cuda_code(e);
+    }
+    if (rc >= 0 && stats) {
+        int r2 = knng_get_stats(c, stats);
+        if (r2) rc = r2;
+    }
+    if (rc >= 0) {
+        int r3 = ctx_check(c);
+        if (r3) rc = r3;
+    }
+    knng_destroy(c);
+    return rc;
 }
 
 int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *rows, int64_t nq, int32_t *ids,

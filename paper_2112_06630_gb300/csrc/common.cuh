@@ -187,6 +187,12 @@ struct DevState {
     int64_t n;
     int d, dp, nv, K, s, R, cap, dpb;
     int bf16;                  // 1: high-d joins use bf16 tensor-core Gram blocks
+    // batched mode (many independent data sets in one node space), else null:
+    const int *ds;             // node -> data set
+    const long long *ds_off;   // data set -> first node
+    const int *ds_n;           // data set -> number of nodes
+    const double *ds_thr;      // data set -> delta * n * K
+    long long *ds_changes;     // data set x kMaxLocalIters change counts
     double thr;                // delta * n * K
 };
 
@@ -203,6 +209,8 @@ constexpr int kChunkPoison = -1;
 // Slot of proposal number `pos` of node p, or nullptr when the bucket or the
 // pool is exhausted (the caller then inserts into the list under its lock).
 __device__ __forceinline__ uint64_t *bucket_slot(const DevState &st, uint32_t p, int pos);
+
+constexpr int kMaxLocalIters = 1024;  // iterations one context can run
 
 // True when iteration `it` must not run because an earlier one converged.
 __device__ __forceinline__ bool iteration_skipped(const DevState &st, int it) {
@@ -232,5 +240,20 @@ __device__ __forceinline__ uint64_t *bucket_slot(const DevState &st, uint32_t p,
     }
     if (c == kChunkPoison) return nullptr;
     return st.ppool + ((size_t)(c - 1) << kBucketRunBits) + off;
+}
+}  // namespace knng
+
+namespace knng {
+// Batched mode: node u's data set converged in an earlier iteration.
+__device__ __forceinline__ bool node_skipped(const DevState &st, long long u, int li) {
+    if (!st.ds || li < 1) return false;
+    const int b = st.ds[u];
+    const volatile long long *ch = st.ds_changes;
+    return (double)ch[(size_t)b * kMaxLocalIters + li - 1] < st.ds_thr[b];
+}
+// node id local to its data set (the random streams are keyed by local ids, so
+// a data set gets the same build alone or batched)
+__device__ __forceinline__ long long node_local(const DevState &st, long long u) {
+    return st.ds ? u - st.ds_off[st.ds[u]] : u;
 }
 }  // namespace knng

@@ -30,6 +30,7 @@ cudaError_t launch_permute(const DevState &src, float *X_dst, uint64_t *keys_dst
 cudaError_t launch_output(const DevState &st, const int32_t *total_perm, const int32_t *total_inv,
                           int32_t *ids, float *dists, cudaStream_t s);
 cudaError_t launch_iota(int32_t *p, int64_t n, cudaStream_t s);
+cudaError_t launch_ds_map(const long long *ds_off, int nds, int64_t n, int *ds, cudaStream_t s);
 cudaError_t launch_invert(const int32_t *perm, int64_t n, int32_t *inv, cudaStream_t s);
 cudaError_t launch_bruteforce(const float *X, int64_t n, int dp, int K, const int64_t *rows, int64_t nq,
                               int32_t *ids, float *dists, cudaStream_t s);

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long u = gw; u < st.n; u += nw) {
+        if (node_skipped(st, u, li)) continue;  // batched: u's data set converged
         // ---- 1. candidates of u, repeats removed (new first, then old)
         int ns, m;
         w_candids += warp_gather_candidates(st, u, raw, hset, sid, ns, m, w_setovf);
@@ -243,6 +244,8 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(DevState st, in
     long long w_ins = 0, w_changes = 0, w_merges = 0;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    int cur_ds = -1;          // batched: changes are added up per data set
+    long long cur_changes = 0;
     for (long long p = gw; p < st.n; p += nw) {
         const int cnt_all = st.pcursor[p];
         if (cnt_all == 0) continue;
@@ -287,11 +290,24 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(DevState st, in
         }
         // entries flagged "inserted in this iteration" that are still listed
         // (the sampling pass cleared that flag everywhere before the join)
-        w_changes += __popc(__ballot_sync(kFull, valid && (Lk & kFlagIns)));
+        const int ch = __popc(__ballot_sync(kFull, valid && (Lk & kFlagIns)));
+        w_changes += ch;
+        if (st.ds) {
+            const int b = st.ds[p];
+            if (b != cur_ds) {
+                if (cur_ds >= 0 && cur_changes && lane == 0)
+                    atomic_add_ll(st.ds_changes + (size_t)cur_ds * kMaxLocalIters + li, cur_changes);
+                cur_ds = b;
+                cur_changes = 0;
+            }
+            cur_changes += ch;
+        }
         if (ins && valid) row[lane] = Lk;
         w_ins += ins;
         ++w_merges;
     }
+    if (cur_ds >= 0 && cur_changes && lane == 0)
+        atomic_add_ll(st.ds_changes + (size_t)cur_ds * kMaxLocalIters + li, cur_changes);
     if (lane == 0) {
         atomic_add_ll(&bstat[0], w_ins);
         atomic_add_ll(&bstat[1], w_changes);

@@ -59,11 +59,15 @@ __global__ void __launch_bounds__(kBlock) init_random_kernel(DevState st, uint64
     const float4 *X4 = reinterpret_cast<const float4 *>(st.X);
     constexpr uint64_t kMaxAttempts = 1ull << 26;
     for (long long u = gwarp(); u < st.n; u += nwarps()) {
+        // batched mode: sample within u's data set, keyed by local ids
+        const long long off = st.ds ? st.ds_off[st.ds[u]] : 0;
+        const uint64_t nb = st.ds ? (uint64_t)st.ds_n[st.ds[u]] : n;
+        const uint64_t ul = (uint64_t)(u - off);
         int have = 0;
         uint64_t a = 0;
         while (have < K) {
-            uint64_t h = hash_uj(base, (uint64_t)u, a + lane);
-            uint32_t v = (uint32_t)(((h >> 32) * n) >> 32);
+            uint64_t h = hash_uj(base, ul, a + lane);
+            uint32_t v = (uint32_t)(off + (long long)(((h >> 32) * nb) >> 32));
             bool ok = v != (uint32_t)u;
             for (int k = 0; k < have; ++k) ok = ok && (chosen[k] != v);
             unsigned same = __match_any_sync(kFull, v);
@@ -78,7 +82,8 @@ __global__ void __launch_bounds__(kBlock) init_random_kernel(DevState st, uint64
             if (a >= kMaxAttempts) {
                 if (lane == 0) atomic_add_ll(&st.stats[kStatInitAttemptsExceeded], 1ll);
                 if (lane == 0) atomicOr(err, 1);
-                for (int k = have + (int)lane; k < K; k += 32) chosen[k] = (uint32_t)((u + 1 + k) % st.n);
+                for (int k = have + (int)lane; k < K; k += 32)
+                    chosen[k] = (uint32_t)(off + (long long)((ul + 1 + k) % nb));
                 have = K;
                 __syncwarp();
             }
@@ -150,6 +155,7 @@ __global__ void count_kernel(DevState st, int li) {
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *st.pool_next = 0;  // bucket pool restarts
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        if (st.ds && node_skipped(st, e / st.K, li)) continue;
         uint64_t key = st.keys[e];
         uint32_t v = key_id(key);
         atomicAdd((key & kFlagNew) ? &st.rev_new[v] : &st.rev_old[v], 1);
@@ -178,6 +184,8 @@ __global__ void __launch_bounds__(kBlock) sample_kernel(DevState st, int li, uin
     const uint32_t s = (uint32_t)st.s;
     long long overflow = 0;
     for (long long u = gwarp(); u < st.n; u += nwarps()) {
+        if (node_skipped(st, u, li)) continue;
+        const uint64_t ul = (uint64_t)node_local(st, u);
         const bool valid = (int)lane < K;
         uint64_t key = valid ? st.keys[(size_t)u * K + lane] : kKeyEmpty;
         const bool isnew = valid && (key & kFlagNew);
@@ -185,7 +193,7 @@ __global__ void __launch_bounds__(kBlock) sample_kernel(DevState st, int li, uin
         const uint32_t cnew = __popc(nm), cold = (uint32_t)K - cnew;
         const uint32_t v = key_id(key);
         bool accf = false;
-        if (valid) accf = accept(hash_uj(fbase, (uint64_t)u, lane), isnew ? cnew : cold, s);
+        if (valid) accf = accept(hash_uj(fbase, ul, lane), isnew ? cnew : cold, s);
         const unsigned mn = __ballot_sync(kFull, accf && isnew);
         const unsigned mo = __ballot_sync(kFull, accf && !isnew);
         if (accf && isnew) st.cand_new[(size_t)u * st.cap + __popc(mn & lanemask_lt())] = (int)v;
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(kBlock) sample_kernel(DevState st, int li, uin
         }
         if (valid) {
             const int rc = isnew ? st.rev_new[v] : st.rev_old[v];
-            if (accept(hash_uj(rbase, (uint64_t)u, lane), (uint32_t)rc, s)) {
+            if (accept(hash_uj(rbase, ul, lane), (uint32_t)rc, s)) {
                 int slot = atomicAdd(isnew ? &st.fill_new[v] : &st.fill_old[v], 1);
                 if (slot < st.R)
                     (isnew ? st.cand_new : st.cand_old)[(size_t)v * st.cap + K + slot] = (int)u;
@@ -308,6 +316,25 @@ cudaError_t launch_permute(const DevState &src, float *X_dst, uint64_t *keys_dst
     return cudaGetLastError();
 }
 
+// node -> data set of a batched context (data sets are contiguous node ranges)
+__global__ void ds_map_kernel(const long long *__restrict__ ds_off, int nds, int64_t n, int *__restrict__ ds) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nds - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (ds_off[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        ds[u] = lo;
+    }
+}
+
+cudaError_t launch_ds_map(const long long *ds_off, int nds, int64_t n, int *ds, cudaStream_t s) {
+    int grid = grid_for((const void *)ds_map_kernel, 256, 0);
+    ds_map_kernel<<<grid, 256, 0, s>>>(ds_off, nds, n, ds);
+    return cudaGetLastError();
+}
+
 __global__ void iota_kernel(int32_t *__restrict__ p, int64_t n) {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
         p[u] = (int32_t)u;
@@ -348,6 +375,7 @@ __global__ void __launch_bounds__(kBlock) output_kernel(DevState st, const int32
             uint32_t v = key_id(st.keys[(size_t)p * K + lane]);
             float dd = l2sq_rows(X4 + (size_t)p * st.nv, X4 + (size_t)v * st.nv, st.nv);
             uint32_t vo = total_inv ? (uint32_t)total_inv[v] : v;
+            if (st.ds) vo -= (uint32_t)st.ds_off[st.ds[u]];  // batched: ids local to the data set
             key = make_key(dd, vo, 0);
         }
         key = warp_sort_u64(key);

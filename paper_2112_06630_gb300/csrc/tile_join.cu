@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_join_kernel(DevState st, in
               t_to = 0;
     __syncthreads();
     for (long long u = blockIdx.x; u < st.n; u += gridDim.x) {
+        if (node_skipped(st, u, li)) continue;  // batched: u's data set converged (uniform in the block)
         // ---- 1. candidates (warp 0)
         if (warp == 0) {
             int ns, m;

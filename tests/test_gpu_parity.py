@@ -309,3 +309,28 @@ def test_clustered_n100k_full_size_sampled_parity():
     ro = metrics.recall(x, oi, ei, rows)
     assert rg >= ro - 0.005, (rg, ro)
     assert st["lock_timeouts"] == 0
+
+
+# ---------------------------------------------------------------- batched ----
+
+def test_batched_matches_oracle_per_data_set_bit_exact():
+    """Many data sets (different n and d, incl. rows below and above 64
+    floats) in one batched build: each result equals the oracle's build of
+    that data set alone, bit for bit (integer data)."""
+    g = np.random.default_rng(4)
+    sets = []
+    for b, (n, d) in enumerate([(700, 8), (1500, 3), (400, 96), (2100, 16), (333, 130), (50, 5)]):
+        sets.append(_int_data(n, d, 6, seed=100 + b))
+    K, rho, delta, iters = 8, 0.5, 0.002, 8
+    outs, st = knng.knng_build_batched([_cuda(x) for x in sets], K, rho, delta, iters, seed=3)
+    for x, (gi, gd) in zip(sets, outs):
+        oi, od, ost = oracle.build_knng(x, K, rho, delta, iters, seed=3)
+        assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+def test_batched_equals_single_builds_float_data():
+    sets = [workloads.gaussian_mixture(n, d, 7, seed=n) for n, d in [(3000, 32), (1200, 96), (5000, 128), (800, 32)]]
+    outs, st = knng.knng_build_batched(sets, 16, 0.5, 0.001, 15, seed=9)     # host in / host out
+    for x, (bi, bd) in zip(sets, outs):
+        si, sd, _ = knng.knng_build(_cuda(x), 16, 0.5, 0.001, 15, seed=9)
+        assert (bi == si.cpu().numpy()).all() and (bd == sd.cpu().numpy()).all()
