@@ -135,6 +135,70 @@ def merge_bytes(st: dict) -> float:
     return st["proposals"] * 8.0 + st["merges"] * 2.0 * st["K"] * 8.0
 
 
+def run_batched(args):
+    """256 independent data sets: one batched build (one launch per step for
+    all data sets) against 256 sequential float32 builds."""
+    import torch
+
+    import paper_2112_06630_gb300 as knng
+    from oracle import metrics
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    cfg = workloads.BATCHED
+    sets = workloads.batched_data(cfg["count"], cfg["seed"])
+    xs = [torch.from_numpy(x).to(device) for x in sets]
+    flags = knng.FLAG_BF16 if args.bf16 else 0
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    K, rho, delta, it = cfg["K"], cfg["rho"], cfg["delta"], cfg["max_iters"]
+
+    def timed(fn):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        out = fn()
+        e.record()
+        torch.cuda.synchronize()
+        return s.elapsed_time(e) / 1e3, out
+
+    batched = lambda: knng.knng_build_batched(xs, K, rho, delta, it, seed=0, flags=flags)
+    sequential = lambda: [knng.knng_build(x, K, rho, delta, it, seed=0) for x in xs]
+    for _ in range(args.warmup):
+        batched()
+    tb, tsq = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            t, (outs, st) = timed(batched)
+            tb.append(t)
+    for _ in range(max(1, min(args.steps, 3))):
+        t, seq = timed(sequential)
+        tsq.append(t)
+    g = np.random.default_rng(1)
+    hits, tot = 0.0, 0
+    for b in g.choice(len(sets), 8, replace=False):
+        rows = g.choice(len(sets[b]), min(250, len(sets[b])), replace=False)
+        bi, _ = knng.knng_bruteforce(xs[b], K, rows=torch.from_numpy(rows).to(device))
+        r = metrics.recall(sets[b], outs[b][0].cpu().numpy(), bi.cpu().numpy(), rows)
+        hits += r * len(rows)
+        tot += len(rows)
+    vb, vs = sum(tb) / len(tb), sum(tsq) / len(tsq)
+    line = {
+        "metric": METRIC, "value": round(vb, 6), "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(vb * 1e3, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f32" if args.bf16 else "f32", "data": "synthetic",
+        "config": {"workload": "batched_256", "datasets": len(sets), "total_n": int(sum(len(x) for x in sets)),
+                   "K": K, "rho": rho, "delta": delta, "max_iters": it, "bf16": bool(args.bf16),
+                   "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
+        "sequential_fp32_s": round(vs, 4), "speedup_vs_sequential": round(vs / vb, 2),
+        "recall_at_k": round(hits / tot, 5), "recall_rows": tot, "dist_evals": st["dist_evals"],
+        "gpu_launches": int(st["kernel_launches"]), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args):
     import torch
 
@@ -305,7 +369,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--reorder", action="store_true", help="Algorithm 1 relabelling after iteration 1")
     ap.add_argument("--bf16", action="store_true", help="bf16 tensor-core dots for d >= 64, float32 re-rank")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS),
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["batched_256"],
                     help="another workload than the headline one (measurement table)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
     args = ap.parse_args()
@@ -314,6 +378,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched_256":
+        run_batched(args)
     else:
         run_gpu(args)
 

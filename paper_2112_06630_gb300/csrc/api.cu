@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -47,6 +48,40 @@ int cuda_code(cudaError_t e) { return e == cudaSuccess ? KNNG_OK : (e == cudaErr
     } while (0)
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Device memory comes from a pool owned by the library (one per device) whose
+// release threshold is unlimited: memory freed by one build stays mapped for
+// the next, instead of being returned at every stream synchronisation (the
+// default pool's behaviour), which made each build re-map its arena.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[256];
+
+cudaError_t lib_malloc(void **p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> g(g_pool_mu);
+        if (!g_pool[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&g_pool[dev], &props);
+            if (e != cudaSuccess) {
+                g_pool[dev] = nullptr;
+                return e;
+            }
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool = g_pool[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 
 int check_args(int64_t n, int d, int K, float rho, float delta) {
     if (n < 2 || n >= (int64_t(1) << 30) - 1) return KNNG_ERR_INVALID_ARG;
@@ -165,7 +200,7 @@ int ctx_alloc(knng_ctx *c) {
     const size_t oE = take(sizeof(int));
     const size_t oXb = c->bf16 ? take(sizeof(uint16_t) * n * c->dpb) : 0;
     const size_t oXn = c->bf16 ? take(sizeof(float) * n) : 0;
-    cudaError_t e = cudaMallocAsync((void **)&c->arena, off, c->stream);
+    cudaError_t e = lib_malloc((void **)&c->arena, off, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_code(e);
@@ -211,7 +246,7 @@ int ctx_stage(knng_ctx *c, const float *data) {
     const float *src = data;
     float *tmp = nullptr;
     if (!is_device_ptr(data)) {
-        KNNG_TRY(cudaMallocAsync((void **)&tmp, bytes, c->stream));
+        KNNG_TRY(lib_malloc((void **)&tmp, bytes, c->stream));
         KNNG_TRY(cudaMemcpyAsync(tmp, data, bytes, cudaMemcpyHostToDevice, c->stream));
         src = tmp;
     }
@@ -389,12 +424,12 @@ int knng_init_from_graph(knng_ctx **out, const float *data, int64_t n, int d, in
     const int32_t *ids_d = ids;
     const uint8_t *new_d = is_new;
     if (!is_device_ptr(ids)) {
-        e = cudaMallocAsync((void **)&dids, nb, c->stream);
+        e = lib_malloc((void **)&dids, nb, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dids, ids, nb, cudaMemcpyHostToDevice, c->stream);
         ids_d = dids;
     }
     if (e == cudaSuccess && !is_device_ptr(is_new)) {
-        e = cudaMallocAsync((void **)&dnew, fb, c->stream);
+        e = lib_malloc((void **)&dnew, fb, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dnew, is_new, fb, cudaMemcpyHostToDevice, c->stream);
         new_d = dnew;
     }
@@ -454,7 +489,7 @@ int knng_get(knng_ctx *c, int32_t *ids, float *dists) {
     float *od = dists;
     unsigned char *tmp = nullptr;
     if (!dev_out) {
-        KNNG_TRY(cudaMallocAsync((void **)&tmp, align256(ib) + db, c->stream));
+        KNNG_TRY(lib_malloc((void **)&tmp, align256(ib) + db, c->stream));
         oi = (int32_t *)tmp;
         od = (float *)(tmp + align256(ib));
     }
@@ -654,7 +689,7 @@ int knng_build_batched(const knng_desc *descs, int count, int K, float rho, floa
     const size_t oDs = take(sizeof(int) * ntot), oOff = take(sizeof(long long) * (count + 1)),
                  oN = take(sizeof(int) * count), oT = take(sizeof(double) * count),
                  oC = take(sizeof(long long) * (size_t)count * kMaxLocalIters);
-    e = cudaMallocAsync((void **)&c->barena, o, s);
+    e = lib_malloc((void **)&c->barena, o, s);
     if (e == cudaSuccess) {
         c->ds = (int *)(c->barena + oDs);
         c->ds_off = (long long *)(c->barena + oOff);
@@ -675,7 +710,7 @@ int knng_build_batched(const knng_desc *descs, int count, int K, float rho, floa
         const float *src = d.data;
         float *tmp = nullptr;
         if (!is_device_ptr(d.data)) {
-            e = cudaMallocAsync((void **)&tmp, sizeof(float) * d.n * d.d, s);
+            e = lib_malloc((void **)&tmp, sizeof(float) * d.n * d.d, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, d.data, sizeof(float) * d.n * d.d, cudaMemcpyHostToDevice, s);
             src = tmp;
         }
@@ -694,8 +729,8 @@ int knng_build_batched(const knng_desc *descs, int count, int K, float rho, floa
     int32_t *oi = nullptr;
     float *od = nullptr;
     if (!rc) {
-        e = cudaMallocAsync((void **)&oi, sizeof(int32_t) * ntot * K, s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&od, sizeof(float) * ntot * K, s);
+        e = lib_malloc((void **)&oi, sizeof(int32_t) * ntot * K, s);
+        if (e == cudaSuccess) e = lib_malloc((void **)&od, sizeof(float) * ntot * K, s);
         if (e == cudaSuccess) e = launch_output(c->dev(false), nullptr, nullptr, oi, od, s);
         c->launches++;
         for (int b = 0; e == cudaSuccess && b < count; ++b) {
@@ -731,14 +766,14 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
     const size_t ib = align256(sizeof(int32_t) * nq * K), db = sizeof(float) * nq * K;
     const bool dev_out = is_device_ptr(ids) && is_device_ptr(dists);
     unsigned char *tmp = nullptr;
-    KNNG_TRY(cudaMallocAsync((void **)&tmp, xb + rb + (dev_out ? 0 : ib + db), s));
+    KNNG_TRY(lib_malloc((void **)&tmp, xb + rb + (dev_out ? 0 : ib + db), s));
     float *X = (float *)tmp;
     int rc = KNNG_OK;
     const float *src = data;
     float *staged = nullptr;
     cudaError_t e = cudaSuccess;
     if (!is_device_ptr(data)) {
-        e = cudaMallocAsync((void **)&staged, sizeof(float) * n * d, s);
+        e = lib_malloc((void **)&staged, sizeof(float) * n * d, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(staged, data, sizeof(float) * n * d, cudaMemcpyHostToDevice, s);
         src = staged;
     }

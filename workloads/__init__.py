@@ -65,31 +65,40 @@ def gaussian_mixture(n: int, d: int, clusters: int, seed: int = 0,
     return x
 
 
-def mnist_like(n: int = 70_000, d: int = 784, seed: int = 0, prototypes: int = 10,
-               proto_on: float = 1.0 / 6.0, flip: float = 0.05,
-               return_labels: bool = False):
-    """MNIST-shaped stand-in: integer intensities 0..255 stored as float32.
+def mnist_like(n: int = 70_000, d: int = 784, seed: int = 0, prototypes: int = 10, latent: int = 6,
+               proto_on: float = 0.20, flip: float = 0.01, return_labels: bool = False):
+    """MNIST-shaped stand-in: integer intensities 0..255 stored as float32,
+    about 80% zeros, points on low-dimensional manifolds around prototypes.
 
-    Recipe: `prototypes` random binary masks, each pixel on with probability
-    `proto_on`, with on-intensities uniform in {128..255}.  A point copies a
-    random prototype, flips every pixel on/off independently with probability
-    `flip`, jitters on pixels by a uniform integer in [-40, 40] and clamps them
-    to [1, 255]; pixels switched on by the flip get a uniform intensity in
-    {64..255}.  With the defaults about 80% of all values are zero
-    (on-fraction = proto_on * (1 - flip) + (1 - proto_on) * flip = 0.20).
+    Recipe: `prototypes` random binary masks (each pixel on with probability
+    `proto_on`) with base intensities uniform in {100..200} and a
+    `latent`-dimensional deformation basis with N(0, 25^2) entries.  A point
+    takes a random prototype, a latent vector z ~ N(0, I), and sets every on
+    pixel to base + basis . z + a uniform integer in [-3, 3], rounded and
+    clamped to [1, 255]; then every pixel is flipped on/off independently with
+    probability `flip` (switched-on pixels get a uniform intensity in
+    {64..255}).  Handwritten digits vary along a few smooth directions around
+    a class shape; so do these points, which keeps nearest neighbours
+    meaningful (pure per-pixel noise would make all same-class points about
+    equally far apart).
     """
     g = _rng(seed)
     masks = g.random((prototypes, d)) < proto_on
-    inten = g.integers(128, 256, size=(prototypes, d))
-    protos = np.where(masks, inten, 0).astype(np.int32)
+    base = g.integers(100, 201, size=(prototypes, d)).astype(np.float64)
+    basis = g.standard_normal((prototypes, d, latent)) * 25.0
     labels = g.integers(0, prototypes, size=n)
-    x = protos[labels].copy()
+    z = g.standard_normal((n, latent))
+    jitter = g.integers(-3, 4, size=(n, d))
+    x = np.empty((n, d), dtype=np.float64)
+    for c in range(prototypes):
+        idx = np.nonzero(labels == c)[0]
+        x[idx] = base[c] + z[idx] @ basis[c].T
+    x = np.clip(np.rint(x + jitter), 1, 255)
+    on = masks[labels]
+    x = np.where(on, x, 0.0)
     flips = g.random((n, d)) < flip
-    jitter = g.integers(-40, 41, size=(n, d))
     fresh = g.integers(64, 256, size=(n, d))
-    on = x > 0
-    x = np.where(on, np.clip(x + jitter, 1, 255), 0)
-    x = np.where(flips & on, 0, x)
+    x = np.where(flips & on, 0.0, x)
     x = np.where(flips & ~on, fresh, x)
     x = x.astype(np.float32)
     if return_labels:
@@ -170,6 +179,15 @@ WORKLOADS = {
                                  "mixture", (("clusters", 1000), ("centre_std", 2.0),
                                              ("sigma", 0.5))),
 }
+
+
+BATCHED = dict(name="batched_256", count=256, K=16, rho=0.5, delta=0.001, max_iters=15, seed=0)
+
+
+def batched_data(count: int = 256, seed: int = 0):
+    """Data sets of the batched workload: equal-weight Gaussian mixtures with
+    the sizes of batched_specs (centres U[-10, 10]^d, sigma 1)."""
+    return [gaussian_mixture(s["n"], s["d"], s["clusters"], seed=s["seed"]) for s in batched_specs(count, seed)]
 
 
 def make(name: str) -> tuple[Workload, np.ndarray]:
