@@ -3,13 +3,14 @@
 //
 // The distance block of a node's candidate set S (|S| <= 64, new ones first)
 // is computed into shared memory as D[i][j] for every new row i and every
-// column j, in passes of 32 new rows.  Candidate rows stream through shared
-// memory in 64-dimension chunks, double-buffered with cp.async.
-//   - float32: each thread owns a 4 x 4 block of pairs and accumulates the
-//     canonical difference form (four partial sums over t mod 4, ascending t,
-//     fused multiply-add), so every value is bit-identical to the warp kernel
-//     and to the rest of the library.  Rows are read by broadcast (i) and by
-//     8-thread phases on an odd float4 stride (j): no bank conflicts.
+// column j.  Candidate rows stream through shared memory in chunks (32
+// floats, or 64 bf16), double-buffered with cp.async.
+//   - float32: one item = one new row and four columns, spread evenly over
+//     the block (only the pairs the node needs), accumulating the canonical
+//     difference form (four partial sums over t mod 4, ascending t, fused
+//     multiply-add), so every value is bit-identical to the warp kernel and to
+//     the rest of the library.  Rows are read by broadcast (i) and by 8-thread
+//     phases on an odd float4 stride (j): no bank conflicts.
 //   - bf16: the Gram block x_i . x_j on the tensor cores (mma.sync
 //     m16n8k16, bf16 in, float32 accumulate; ldmatrix on a 144-byte row
 //     stride), then d = |x_i|^2 + |x_j|^2 - 2 x_i . x_j with the norms of the
@@ -22,6 +23,7 @@
 // from D; full buckets take the locked way.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "join_common.cuh"
@@ -30,8 +32,9 @@ namespace knng {
 
 namespace {
 constexpr int kTileThreads = 128;
-constexpr int kChunkV = 16;                  // float4 per row chunk (64 floats)
+constexpr int kChunkV = 8;                   // float4 per row chunk (32 floats)
 constexpr int kStrideV = kChunkV + 1;        // odd float4 stride
+constexpr int kItemsPerThread = 2;           // (new row, 4 columns) items per thread and pass
 constexpr int kChunkB = 64;                  // bf16 per row chunk
 constexpr int kStrideB = kChunkB + 8;        // 144-byte rows for ldmatrix
 constexpr int kDStride = kSetMax + 1;
@@ -45,7 +48,6 @@ struct TileSmem {
     unsigned long long mask[kSetMax];
     float nrm[kSetMax];
     float D[kSetMax * kDStride];
-    uint64_t L[kSetMax * (kMaxK + 1)];  // snapshots of the targets' lists
     unsigned long long ovf;
     int ovf_from[kSetMax];
     int ns, m;
@@ -83,44 +85,60 @@ __device__ __forceinline__ void stage_b16(uint16_t *buf, const uint16_t *Xb, con
     cp_async_commit();
 }
 
-// D[i][j] for i in [r0, min(r0 + 32, m)), j < ns: canonical float32 form
-__device__ void tile_dist_f32(TileSmem &sm, float4 *stage, const float4 *X4, int nv, int ns, int m, int r0) {
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    Acc4 acc[4][4];
+// D[i][j] for every new row i < m and column j < ns, canonical float32 form.
+// Work item = one row i and the four columns jq, jq + JQ, jq + 2 JQ, jq + 3 JQ
+// (JQ = ceil(ns / 4)); items are spread over the block, up to two per thread
+// per pass.  Consecutive threads take consecutive columns, which are distinct
+// rows on an odd float4 stride: conflict-free 8-thread phases; row i is read
+// by broadcast.
+__device__ void tile_dist_f32(TileSmem &sm, float4 *stage, const float4 *X4, int nv, int ns, int m) {
+    const int tid = threadIdx.x;
+    const int JQ = (ns + 3) >> 2, items = m * JQ;
     const int nchunks = (nv + kChunkV - 1) / kChunkV;
     float4 *buf[2] = {stage, stage + kSetMax * kStrideV};
-    stage_f32(buf[0], X4, sm.sid, ns, nv, 0);
-    for (int c = 0; c < nchunks; ++c) {
-        if (c + 1 < nchunks) {
-            stage_f32(buf[(c + 1) & 1], X4, sm.sid, ns, nv, c + 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+    for (int it0 = 0; it0 < items; it0 += kTileThreads * kItemsPerThread) {
+        Acc4 acc[kItemsPerThread][4];
+        int ii[kItemsPerThread], jj[kItemsPerThread];
+#pragma unroll
+        for (int w = 0; w < kItemsPerThread; ++w) {
+            const int item = it0 + w * kTileThreads + tid;
+            ii[w] = item < items ? item / JQ : -1;
+            jj[w] = item < items ? item - ii[w] * JQ : 0;
         }
-        __syncthreads();
-        const float4 *b = buf[c & 1];
-        const int vc = min(kChunkV, nv - c * kChunkV);
-        for (int v = 0; v < vc; ++v) {
-            float4 a[4], bj[4];
+        stage_f32(buf[0], X4, sm.sid, ns, nv, 0);
+        for (int c = 0; c < nchunks; ++c) {
+            if (c + 1 < nchunks) {
+                stage_f32(buf[(c + 1) & 1], X4, sm.sid, ns, nv, c + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const float4 *b = buf[c & 1];
+            const int vc = min(kChunkV, nv - c * kChunkV);
+#pragma unroll
+            for (int w = 0; w < kItemsPerThread; ++w) {
+                if (ii[w] < 0) continue;
+                const float4 *ri = b + ii[w] * kStrideV;
+                const float4 *rj = b + jj[w] * kStrideV;
+                for (int v = 0; v < vc; ++v) {
+                    const float4 a = ri[v];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[w][q].add(a, rj[q * JQ * kStrideV + v]);
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int w = 0; w < kItemsPerThread; ++w) {
+            if (ii[w] < 0) continue;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                a[q] = b[(r0 + ty + 8 * q) * kStrideV + v];
-                bj[q] = b[(tx + 16 * q) * kStrideV + v];
+                const int j = jj[w] + q * JQ;
+                if (j < ns) sm.D[ii[w] * kDStride + j] = acc[w][q].sum();
             }
-#pragma unroll
-            for (int qi = 0; qi < 4; ++qi)
-#pragma unroll
-                for (int qj = 0; qj < 4; ++qj) acc[qi][qj].add(a[qi], bj[qj]);
         }
-        __syncthreads();
     }
-#pragma unroll
-    for (int qi = 0; qi < 4; ++qi)
-#pragma unroll
-        for (int qj = 0; qj < 4; ++qj) {
-            const int i = r0 + ty + 8 * qi, j = tx + 16 * qj;
-            if (i < m && j < ns) sm.D[i * kDStride + j] = acc[qi][qj].sum();
-        }
 }
 
 // D[i][j] for i in [r0, min(r0 + 32, m)), j < ns: bf16 tensor-core Gram block
@@ -144,14 +162,17 @@ __device__ void tile_dist_b16(TileSmem &sm, uint16_t *stage, const uint16_t *Xb,
         }
         __syncthreads();
         const uint16_t *b = buf[c & 1];
+        const bool rows_live = r0 + mt * 16 < m;
 #pragma unroll
         for (int ks = 0; ks < kChunkB / 16; ++ks) {
+            if (!rows_live) break;  // warp-uniform: this warp's 16 rows are all past m
             uint32_t a0, a1, a2, a3;
             asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                          : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
                          : "r"(smem_u32(b + arow * kStrideB + ks * 16 + acol)));
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+                if ((nt0 + q) * 8 >= ns) break;  // warp-uniform: columns past the set
                 uint32_t b0, b1;
                 asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
                              : "=r"(b0), "=r"(b1)
@@ -210,12 +231,12 @@ __global__ void __launch_bounds__(kTileThreads) tile_join_kernel(DevState st, in
                 if (kBF16) sm.nrm[i] = st.xnorm[sm.sid[i]];
             }
             __syncthreads();
-            // ---- 3. distance block, passes of 32 new rows
-            for (int r0 = 0; r0 < m; r0 += 32) {
-                if (kBF16)
+            // ---- 3. distance block
+            if (kBF16) {
+                for (int r0 = 0; r0 < m; r0 += 32)
                     tile_dist_b16(sm, reinterpret_cast<uint16_t *>(stage_mem), st.Xb, st.dpb, ns, m, r0);
-                else
-                    tile_dist_f32(sm, reinterpret_cast<float4 *>(stage_mem), X4, nv, ns, m, r0);
+            } else {
+                tile_dist_f32(sm, reinterpret_cast<float4 *>(stage_mem), X4, nv, ns, m);
             }
             __syncthreads();
             if (tid == 0) {
@@ -252,15 +273,16 @@ __global__ void __launch_bounds__(kTileThreads) tile_join_kernel(DevState st, in
             //         out by K better keys).  float32: a pair has one key, so
             //         "listed" is "the same (dist, id) at its lower bound";
             //         bf16: the id is searched.
+            uint64_t *Lsnap = reinterpret_cast<uint64_t *>(stage_mem);  // the row stage is free now
             for (int e = tid; e < ns * K; e += kTileThreads) {
                 const int t = e / K, k = e - t * K;
-                if (sm.mask[t]) sm.L[t * (kMaxK + 1) + k] = __ldcg(st.keys + (size_t)sm.sid[t] * K + k);
+                if (sm.mask[t]) Lsnap[t * (kMaxK + 1) + k] = __ldcg(st.keys + (size_t)sm.sid[t] * K + k);
             }
             __syncthreads();
             for (int t = tid; t < ns; t += kTileThreads) {
                 unsigned long long mt = sm.mask[t];
                 if (!mt) continue;
-                const uint64_t *Lt = sm.L + t * (kMaxK + 1);
+                const uint64_t *Lt = Lsnap + t * (kMaxK + 1);
                 const uint64_t worst = Lt[K - 1];
                 for (unsigned long long mm = mt; mm; mm &= mm - 1) {
                     const int j = __ffsll((long long)mm) - 1;
@@ -370,7 +392,9 @@ __global__ void __launch_bounds__(kTileThreads) tile_join_kernel(DevState st, in
 namespace {
 template <bool kBF16>
 cudaError_t launch_tile_t(const DevState &st, int li, cudaStream_t s) {
-    const size_t dyn = kBF16 ? 2ull * kSetMax * kStrideB * sizeof(uint16_t) : 2ull * kSetMax * kStrideV * 16;
+    // two row-chunk buffers, later reused for the targets' list snapshots
+    size_t dyn = kBF16 ? 2ull * kSetMax * kStrideB * sizeof(uint16_t) : 2ull * kSetMax * kStrideV * 16;
+    dyn = std::max(dyn, (size_t)kSetMax * (kMaxK + 1) * sizeof(uint64_t));
     auto kern = tile_join_kernel<kBF16>;
     static bool opted_in = false;
     if (!opted_in) {
