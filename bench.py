@@ -216,7 +216,8 @@ def run_gpu(args):
     xd = torch.from_numpy(x).to(device)
     stream = torch.cuda.current_stream(device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
-    flags = (knng.FLAG_REORDER if args.reorder else 0) | (knng.FLAG_BF16 if args.bf16 else 0)
+    flags = (knng.FLAG_REORDER if args.reorder else 0) | (knng.FLAG_BF16 if args.bf16 else 0) | \
+        (knng.FLAG_GRAPH if args.graph else 0)
     dp = (w.d + 3) // 4 * 4
     if args.bf16 and w.d >= 64:
         dp = (w.d + 63) // 64 * 64 // 2  # bf16 rows: half the bytes of float32
@@ -249,7 +250,9 @@ def run_gpu(args):
     # library on the launching stream, algorithmic bytes from device counters
     flush.fill_(1)
     torch.cuda.synchronize()
-    _, _, tst = build(knng.FLAG_TIMING)
+    # (events inside a captured graph cannot be timed: this build runs ungraphed)
+    _, _, tst = knng.knng_build(xd, w.K, w.rho, w.delta, w.max_iters, seed=0,
+                                flags=(flags & ~knng.FLAG_GRAPH) | knng.FLAG_TIMING)
     torch.cuda.synchronize()
 
     # end to end through the public API: pinned host input, host outputs
@@ -304,7 +307,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if args.bf16 else "f32", "data": "synthetic",
         "config": {"workload": args.workload, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
                    "max_iters": w.max_iters, "reorder": bool(args.reorder), "bf16": bool(args.bf16),
-                   "parallelism": f"replicas{ws}",
+                   "graph": bool(args.graph), "parallelism": f"replicas{ws}",
                    "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
         "recall_at_k": round(rec, 5), "recall_rows": RECALL_ROWS,
         "iterations": stats["iterations"], "dist_evals": stats["dist_evals"],
@@ -369,6 +372,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--reorder", action="store_true", help="Algorithm 1 relabelling after iteration 1")
     ap.add_argument("--bf16", action="store_true", help="bf16 tensor-core dots for d >= 64, float32 re-rank")
+    ap.add_argument("--graph", action="store_true", help="launch the iteration loop as one captured CUDA graph")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["batched_256"],
                     help="another workload than the headline one (measurement table)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")

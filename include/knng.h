@@ -57,7 +57,7 @@ extern "C" {
 #define KNNG_FLAG_REORDER 0x1u   /* Algorithm 1 (list of the node on spot i) + relabel after iteration 1 */
 #define KNNG_FLAG_REORDER_B 0x2u /* with REORDER: the literal reading (list of node i) */
 #define KNNG_FLAG_TIMING 0x4u    /* record CUDA events around every local-join and list-merge launch */
-#define KNNG_FLAG_GRAPH 0x8u     /* knng_run: replay the iteration loop as one CUDA graph */
+#define KNNG_FLAG_GRAPH 0x8u     /* knng_run: capture the iteration loop as one CUDA graph and launch it */
 #define KNNG_FLAG_BF16 0x10u     /* d >= 64: local-join dots in bf16 on the tensor cores (float32
                                     accumulate, |x|^2+|y|^2-2x.y); output re-ranked in float32 */
 
@@ -141,7 +141,9 @@ int knng_iterate(knng_ctx *ctx, int64_t *changes_out);
 /*
  * Enqueue up to max_iters iterations without host round trips: each iteration's
  * kernels skip themselves on the device once a previous iteration's change count
- * fell below delta * n * K.  Does not synchronise.
+ * fell below delta * n * K.  With KNNG_FLAG_GRAPH the loop is captured (stream
+ * capture, thread-local mode) and launched as one CUDA graph.  Does not
+ * synchronise.
  */
 int knng_run(knng_ctx *ctx, int max_iters);
 

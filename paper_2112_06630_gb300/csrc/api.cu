@@ -39,7 +39,13 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int cuda_code(cudaError_t e) { return e == cudaSuccess ? KNNG_OK : (e == cudaErrorMemoryAllocation ? KNNG_ERR_OOM : KNNG_ERR_CUDA); }
+// Maps a CUDA error to a return code and clears it as the thread's last error,
+// so that a failed call does not fail the next, unrelated launch check.
+int cuda_code(cudaError_t e) {
+    if (e == cudaSuccess) return KNNG_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? KNNG_ERR_OOM : KNNG_ERR_CUDA;
+}
 
 #define KNNG_TRY(expr)                              \
     do {                                            \
@@ -125,6 +131,9 @@ struct knng_ctx {
     int *ds = nullptr, *ds_n = nullptr;
     long long *ds_off = nullptr, *ds_changes = nullptr;
     double *ds_thr = nullptr;
+
+    std::vector<cudaGraphExec_t> graphs;  // captured iteration loops (KNNG_FLAG_GRAPH)
+    cudaStream_t capture = nullptr;       // private stream the loops are captured on
 
     std::vector<cudaEvent_t> ev;  // start/stop pairs around join launches
     std::vector<int> ev_li;       // iteration index of each pair
@@ -469,10 +478,37 @@ int knng_iterate(knng_ctx *c, int64_t *changes_out) {
 
 int knng_run(knng_ctx *c, int max_iters) {
     if (!c || max_iters < 0 || max_iters > kMaxItersArg) return KNNG_ERR_INVALID_ARG;
-    for (int t = 0; t < max_iters; ++t) {
-        int rc = enqueue_iteration(c, true);
-        if (rc) return rc;
+    const bool graph = (c->flags & KNNG_FLAG_GRAPH) && max_iters > 0;
+    if (!graph) {
+        for (int t = 0; t < max_iters; ++t) {
+            int rc = enqueue_iteration(c, true);
+            if (rc) return rc;
+        }
+        return KNNG_OK;
     }
+    // The whole loop (every kernel of every iteration, skipping itself on the
+    // device after convergence) becomes one graph, captured on a private
+    // stream (the caller's may be the legacy stream, which cannot be
+    // captured) and launched on the caller's stream.
+    if (!c->capture) KNNG_TRY(cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
+    cudaStream_t user = c->stream;
+    KNNG_TRY(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+    c->stream = c->capture;
+    int rc = KNNG_OK;
+    for (int t = 0; t < max_iters && !rc; ++t) rc = enqueue_iteration(c, true);
+    c->stream = user;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->capture, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : cuda_code(e);
+    }
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_code(e);
+    c->graphs.push_back(ge);
+    KNNG_TRY(cudaGraphLaunch(ge, c->stream));
     return KNNG_OK;
 }
 
@@ -621,6 +657,11 @@ int knng_get_stats(knng_ctx *c, knng_stats *out) {
 
 int knng_destroy(knng_ctx *c) {
     if (!c) return KNNG_OK;
+    if (!c->graphs.empty()) {
+        cudaStreamSynchronize(c->stream);  // executable graphs may still run
+        for (cudaGraphExec_t g : c->graphs) cudaGraphExecDestroy(g);
+    }
+    if (c->capture) cudaStreamDestroy(c->capture);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->arena) cudaFreeAsync(c->arena, c->stream);
     if (c->barena) cudaFreeAsync(c->barena, c->stream);

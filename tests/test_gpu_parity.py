@@ -271,6 +271,14 @@ def test_uniform_n2k_recall_and_invariants():
     assert abs(rg - ro) <= 0.005
 
 
+def test_graph_capture_gives_the_same_graph():
+    x = workloads.gaussian_mixture(4000, 16, 12, seed=6)
+    a_i, a_d, sa = knng.knng_build(_cuda(x), 12, 0.5, 0.001, 10, seed=1)
+    b_i, b_d, sb = knng.knng_build(_cuda(x), 12, 0.5, 0.001, 10, seed=1, flags=knng.FLAG_GRAPH)
+    assert (a_i.cpu().numpy() == b_i.cpu().numpy()).all() and (a_d.cpu().numpy() == b_d.cpu().numpy()).all()
+    assert sa["iterations"] == sb["iterations"] and sa["dist_evals"] == sb["dist_evals"]
+
+
 def test_host_and_device_pointers_agree():
     x = workloads.gaussian_mixture(3000, 16, 10, seed=1)
     hi, hd, _ = knng.knng_build(x, 10, 0.5, 0.001, 8, seed=2)             # host in/out
