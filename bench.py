@@ -50,8 +50,39 @@ def _peaks():
         return None
 
 
+class _Nvml:
+    """Minimal in-process NVML reader (ctypes): SM clock, max SM clock and the
+    clock-event reasons, without spawning a process per sample."""
+
+    HW_SLOWDOWN, SW_POWER_CAP = 0x8, 0x4
+    HW_THERMAL, SW_THERMAL = 0x40, 0x20
+
+    def __init__(self, index: int):
+        import ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        self.c = ctypes
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+
+    def sample(self):
+        c = self.c
+        sm, mx, reasons = c.c_uint(), c.c_uint(), c.c_ulonglong()
+        self.lib.nvmlDeviceGetClockInfo(self.h, 1, c.byref(sm))            # NVML_CLOCK_SM
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, c.byref(mx))
+        self.lib.nvmlDeviceGetCurrentClocksEventReasons(self.h, c.byref(reasons))
+        r = reasons.value
+        names = [nm for nm, bit in (("hw_slowdown", self.HW_SLOWDOWN), ("hw_thermal_slowdown", self.HW_THERMAL),
+                                    ("sw_thermal_slowdown", self.SW_THERMAL), ("sw_power_cap", self.SW_POWER_CAP))
+                 if r & bit]
+        return float(sm.value), float(mx.value), names
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """SM clocks and throttle reasons sampled during the timed region: NVML in
+    process every 10 ms (nvidia-smi every 200 ms if NVML cannot be loaded)."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -59,21 +90,29 @@ class ClockSampler:
 
     def __init__(self, index: int):
         self.index = index
-        self.rows = []
+        self.samples = []  # (sm_mhz, max_mhz, [reasons])
         self._stop = threading.Event()
         self._t = None
+        try:
+            self.nvml = _Nvml(index)
+        except Exception:
+            self.nvml = None
+
+    def _smi(self):
+        out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=5).stdout.strip()
+        r = [c.strip() for c in out.split(",")]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        return (float(r[1]), float(r[2]), [nm for nm, v in zip(names, r[5:9]) if v.lower() == "active"])
 
     def _run(self):
         while not self._stop.is_set():
             try:
-                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.rows.append([c.strip() for c in out.split(",")])
+                self.samples.append(self.nvml.sample() if self.nvml else self._smi())
             except Exception:
                 pass
-            self._stop.wait(0.2)
+            self._stop.wait(0.01 if self.nvml else 0.2)
 
     def __enter__(self):
         self._t = threading.Thread(target=self._run, daemon=True)
@@ -85,17 +124,12 @@ class ClockSampler:
         self._t.join(timeout=10)
 
     def summary(self):
-        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
-        reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            if len(r) > 8:
-                for nm, v in zip(names, r[5:9]):
-                    if v.strip().lower() == "active":
-                        reasons.add(nm)
+        sm = [x[0] for x in self.samples]
+        mx = [x[1] for x in self.samples]
+        reasons = sorted({r for x in self.samples for r in x[2]})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(self.samples),
+                "source": "nvml" if self.nvml else "nvidia-smi"}
 
 
 def _dist():

@@ -38,6 +38,7 @@ namespace {
 constexpr int kJoinWarps = 4;
 constexpr int kMergeWarps = 8;
 constexpr int kTileMinNv = 16;  // rows longer than 64 floats go to the tile kernel
+constexpr int kSortMergeMin = 6; // candidates per 32-key batch from which a sort-merge beats insertions
 
 struct JoinLayout {
     int raw_max;      // ints for raw candidate ids
@@ -232,9 +233,59 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
     }
 }
 
+// Merge of up to 32 candidate keys (one per lane, kKeyEmpty = none; none is
+// listed and all order before the worst entry) into the list held one entry
+// per lane: bitonic sort of the candidates, repeats dropped (a pair has one
+// key, so a repeated id is a repeated key, adjacent after sorting), then every
+// element goes to rank "own rank + elements of the other sequence before it"
+// (two binary searches over lanes), scattered through shared memory.  The K
+// smallest of list and candidates stay.  Returns the number of candidates
+// that entered.
+__device__ __forceinline__ int warp_sort_merge(uint64_t &Lk, uint64_t x, int K, uint64_t *scratch) {
+    const unsigned lane = lane_id();
+    x = warp_sort_u64(x);
+    const uint64_t prev = __shfl_up_sync(kFull, x, 1);
+    const bool valid = x != kKeyEmpty && (lane == 0 || key_order(prev) != key_order(x));
+    const unsigned vm = __ballot_sync(kFull, valid);
+    // list entry k: candidates ordered before it (lower bound over all 32 lanes,
+    // then the dropped repeats below that bound removed)
+    int lo = 0, hi = 32;
+#pragma unroll
+    for (int step = 0; step < 6; ++step) {
+        const int mid = (lo + hi) >> 1;
+        const uint64_t cm = __shfl_sync(kFull, x, mid & 31);
+        if (lo < hi) {
+            if (cm < Lk) lo = mid + 1;
+            else hi = mid;
+        }
+    }
+    const int rank_l = (int)lane + __popc(vm & ((lo >= 32) ? 0xFFFFFFFFu : ((1u << lo) - 1u)));
+    // candidate: list entries ordered before it
+    int a = 0, b = K;
+#pragma unroll
+    for (int step = 0; step < 6; ++step) {
+        const int mid = (a + b) >> 1;
+        const uint64_t lm = __shfl_sync(kFull, Lk, mid < K ? mid : K - 1);
+        if (a < b) {
+            if (lm < x) a = mid + 1;
+            else b = mid;
+        }
+    }
+    const int rank_c = __popc(vm & lanemask_lt()) + a;
+    __syncwarp();
+    if ((int)lane < K && rank_l < K) scratch[rank_l] = Lk;
+    if (valid && rank_c < K) scratch[rank_c] = x;
+    __syncwarp();
+    if ((int)lane < K) Lk = scratch[lane];
+    __syncwarp();
+    return __popc(__ballot_sync(kFull, valid && rank_c < K));
+}
+
 // One warp per node with proposals: merge its bucket into its list.
 __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(DevState st, int li) {
     if (iteration_skipped(st, li)) return;
+    __shared__ uint64_t scratch_all[kMergeWarps][kMaxK];
+    uint64_t *scratch = scratch_all[threadIdx.x >> 5];
     __shared__ long long bstat[3];
     if (threadIdx.x < 3) bstat[threadIdx.x] = 0;
     __syncthreads();
@@ -284,9 +335,19 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(DevState st, in
                     else hi = mid;
                 }
             }
-            const bool listed = key_order(__shfl_sync(kFull, Lk, lo)) == xo;
+            bool listed = key_order(__shfl_sync(kFull, Lk, lo)) == xo;
+            if (st.bf16) {
+                // bf16 keys of a pair may differ from its float32 key in the
+                // list: look the id up
+                const uint32_t xi = key_id(x);
+                for (int k = 0; k < K; ++k) listed |= key_id(__shfl_sync(kFull, Lk, k)) == xi;
+            }
             unsigned cand = __ballot_sync(kFull, x < __shfl_sync(kFull, Lk, K - 1) && !listed);
-            for (; cand; cand &= cand - 1) ins += warp_insert(Lk, __shfl_sync(kFull, x, __ffs(cand) - 1), K);
+            if (__popc(cand) >= kSortMergeMin) {
+                ins += warp_sort_merge(Lk, ((cand >> lane) & 1u) ? x : kKeyEmpty, K, scratch);
+            } else {
+                for (; cand; cand &= cand - 1) ins += warp_insert(Lk, __shfl_sync(kFull, x, __ffs(cand) - 1), K);
+            }
         }
         // entries flagged "inserted in this iteration" that are still listed
         // (the sampling pass cleared that flag everywhere before the join)
