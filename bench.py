@@ -169,6 +169,23 @@ def merge_bytes(st: dict) -> float:
     return st["proposals"] * 8.0 + st["merges"] * 2.0 * st["K"] * 8.0
 
 
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu record in
+    profiles/traffic.json, or None when the kernel's sources changed since the
+    capture (their sha256 no longer matches) or no record exists."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        h = hashlib.sha256()
+        for p in rec["sources"]:
+            h.update(open(os.path.join(ROOT, p), "rb").read())
+        if h.hexdigest() != rec["sources_sha256"]:
+            return None
+        return rec["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def run_batched(args):
     """256 independent data sets: one batched build (one launch per step for
     all data sets) against 256 sequential float32 builds."""
@@ -323,8 +340,9 @@ def run_gpu(args):
     jb = kern[name][0] / ran
     jt = kern[name][1] / 1e3 / ran
     achieved = jb / jt / 1e9
+    traffic = measured_traffic(name) if args.workload == WORKLOAD and not args.bf16 else None
     roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
-            "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+            "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
             "peak_source": "measured" if peaks else "fallback",
             "bytes_per_launch": round(jb), "launch_ms": round(jt * 1e3, 4), "launches": ran,
             "time_share_join_merge": [round(tst["join_ms_ran"], 3), round(tst["merge_ms_ran"], 3)]}
