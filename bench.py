@@ -263,7 +263,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
 
-    w, x = workloads.make(args.workload)
+    w, x, wname = _workload(args)
     xd = torch.from_numpy(x).to(device)
     stream = torch.cuda.current_stream(device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
@@ -340,7 +340,7 @@ def run_gpu(args):
     jb = kern[name][0] / ran
     jt = kern[name][1] / 1e3 / ran
     achieved = jb / jt / 1e9
-    traffic = measured_traffic(name) if args.workload == WORKLOAD and not args.bf16 else None
+    traffic = measured_traffic(name) if wname == WORKLOAD and not args.bf16 else None
     roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
             "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
             "peak_source": "measured" if peaks else "fallback",
@@ -357,7 +357,7 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 6), "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if args.bf16 else "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
+        "config": {"workload": wname, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
                    "max_iters": w.max_iters, "reorder": bool(args.reorder), "bf16": bool(args.bf16),
                    "graph": bool(args.graph), "parallelism": f"replicas{ws}",
                    "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
@@ -391,11 +391,23 @@ def cpu_baseline(w, x, builds: int = 1):
             "sample": f"whole workload ({w.n} points), {builds} build(s), single thread"}
 
 
+def _workload(args):
+    """The named workload with the command-line overrides applied (smaller n
+    for profiling captures; rho, delta, iteration cap for recall sweeps)."""
+    import dataclasses
+    w = workloads.WORKLOADS[args.workload]
+    over = {k: v for k, v in (("n", args.n), ("rho", args.rho), ("delta", args.delta),
+                              ("max_iters", args.max_iters)) if v is not None}
+    if over:
+        w = dataclasses.replace(w, **over)
+    return w, w.data(), (args.workload + "".join(f"_{k}{v}" for k, v in over.items()))
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    w, x = workloads.make(args.workload)
+    w, x, wname = _workload(args)
     import oracle
     oracle._load()
     for _ in range(args.warmup):
@@ -407,7 +419,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 2),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
+        "config": {"workload": wname, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
                    "max_iters": w.max_iters, "parallelism": "cpu1"},
         "cpu_baseline": {"value": round(v, 4), "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"whole workload ({w.n} points) per step, single thread"},
@@ -428,6 +440,10 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["batched_256"],
                     help="another workload than the headline one (measurement table)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
+    ap.add_argument("--n", type=int, default=None, help="override the workload's point count (profiling)")
+    ap.add_argument("--rho", type=float, default=None, help="override the sample rate (recall sweeps)")
+    ap.add_argument("--delta", type=float, default=None, help="override the termination threshold")
+    ap.add_argument("--max-iters", type=int, default=None, help="override the iteration cap")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         print("note: at least 3 warm-up steps are required; using 3", file=sys.stderr)
@@ -435,6 +451,8 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched_256":
+        if any(v is not None for v in (args.n, args.rho, args.delta, args.max_iters)):
+            ap.error("--n/--rho/--delta/--max-iters do not apply to the batched workload")
         run_batched(args)
     else:
         run_gpu(args)
