@@ -85,7 +85,8 @@ typedef struct knng_stats {
     int32_t join_launches;     /* local-join launches timed (KNNG_FLAG_TIMING) */
     double join_ms;            /* their summed CUDA-event time */
     int32_t join_ran;          /* timed launches whose iteration ran (not skipped) */
-    int32_t reserved;
+    int32_t join_path;         /* local-join kernel: 0 warp per node (float32 rows of up to 64
+                                  floats), 1 block-per-node tiles, 2 TMA-staged ring */
     double join_ms_ran;        /* summed join-kernel time of those iterations */
     double merge_ms_ran;       /* summed list-merge-kernel time of those iterations */
 } knng_stats;

@@ -46,7 +46,7 @@ class Stats(ctypes.Structure):
         ("lock_timeouts", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("cand_ids", ctypes.c_int64), ("proposals", ctypes.c_int64), ("bucket_overflow", ctypes.c_int64), ("reordered", ctypes.c_int32),
         ("join_launches", ctypes.c_int32), ("join_ms", ctypes.c_double), ("join_ran", ctypes.c_int32),
-        ("reserved", ctypes.c_int32), ("join_ms_ran", ctypes.c_double), ("merge_ms_ran", ctypes.c_double),
+        ("join_path", ctypes.c_int32), ("join_ms_ran", ctypes.c_double), ("merge_ms_ran", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:

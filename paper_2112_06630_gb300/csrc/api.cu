@@ -13,6 +13,7 @@
 
 #include "../../include/knng.h"
 #include "internal.h"
+#include "join_common.cuh"
 
 using namespace knng;
 
@@ -121,6 +122,8 @@ struct knng_ctx {
     float *xnorm = nullptr, *xnorm2 = nullptr;
     int dpb = 0;
     bool bf16 = false;
+    int join_path = kJoinWarp;
+    int *cset = nullptr, *cmeta = nullptr;
     uint64_t *pbucket = nullptr, *ppool = nullptr;
     int32_t *sigma = nullptr, *sigma_inv = nullptr, *total_perm = nullptr, *total_inv = nullptr;
     long long *stats = nullptr, *it_stats = nullptr;
@@ -177,6 +180,9 @@ struct knng_ctx {
         st.ds_n = ds_n;
         st.ds_thr = ds_thr;
         st.ds_changes = ds_changes;
+        st.cset = cset;
+        st.cmeta = cmeta;
+        st.join_path = join_path;
         return st;
     }
 };
@@ -209,6 +215,9 @@ int ctx_alloc(knng_ctx *c) {
     const size_t oE = take(sizeof(int));
     const size_t oXb = c->bf16 ? take(sizeof(uint16_t) * n * c->dpb) : 0;
     const size_t oXn = c->bf16 ? take(sizeof(float) * n) : 0;
+    const bool ring = c->join_path == kJoinRing;
+    const size_t oCs = ring ? take(sizeof(int) * (size_t)n * kSetMax) : 0;
+    const size_t oCm = ring ? take(sizeof(int) * (size_t)n) : 0;
     cudaError_t e = lib_malloc((void **)&c->arena, off, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -240,6 +249,10 @@ int ctx_alloc(knng_ctx *c) {
     if (c->bf16) {
         c->Xb = (uint16_t *)(a + oXb);
         c->xnorm = (float *)(a + oXn);
+    }
+    if (ring) {
+        c->cset = (int *)(a + oCs);
+        c->cmeta = (int *)(a + oCm);
     }
     KNNG_TRY(cudaMemsetAsync(c->locks, 0, sizeof(int) * nint, c->stream));
     KNNG_TRY(cudaMemsetAsync(c->ibuf, 0, sizeof(int) * 6 * n, c->stream));
@@ -299,6 +312,15 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
     // bf16 tensor-core dots where the contraction is long enough to pay
     c->bf16 = (flags & KNNG_FLAG_BF16) && d >= 64;
     c->dpb = (d + 63) & ~63;
+    // test hook: run another join kernel the context can use (parity of the
+    // three kernels on the same inputs)
+    int force = -1;
+    if (const char *e = std::getenv("KNNG_TEST_JOIN_PATH")) {
+        if (!std::strcmp(e, "warp")) force = kJoinWarp;
+        else if (!std::strcmp(e, "tile")) force = kJoinTile;
+        else if (!std::strcmp(e, "ring")) force = kJoinRing;
+    }
+    c->join_path = choose_join_path(c->bf16, c->nv, c->dpb, K, force);
     c->stream = (cudaStream_t)stream;
     c->thr = (double)delta * (double)n * (double)K;
     rc = ctx_alloc(c);
@@ -367,7 +389,7 @@ int enqueue_iteration(knng_ctx *c, bool gate) {
     if (timing) KNNG_TRY(cudaEventRecord(ev[1], c->stream));
     KNNG_TRY(launch_merge(st, li, c->stream));
     if (timing) KNNG_TRY(cudaEventRecord(ev[2], c->stream));
-    c->launches += 4;
+    c->launches += 3 + join_launches(c->join_path);
     c->li++;
     c->it_done++;
     if ((c->flags & KNNG_FLAG_REORDER) && !c->reordered && it == 1) {
@@ -627,6 +649,7 @@ int knng_get_stats(knng_ctx *c, knng_stats *out) {
     out->lock_timeouts = st[kStatLockTimeout];
     out->kernel_launches = c->launches;
     out->reordered = c->reordered ? 1 : 0;
+    out->join_path = c->join_path;
     out->cand_ids = 0;
     out->proposals = 0;
     for (int i = 0; i < c->li; ++i) {

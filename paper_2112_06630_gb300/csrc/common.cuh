@@ -64,17 +64,34 @@ __device__ __forceinline__ bool accept(uint64_t h, uint32_t cnt, uint32_t s) {
 // (s0 + s1) + (s2 + s3).  Every float32 distance in the library (init, join,
 // brute force, re-rank) uses exactly this order, so one pair always gets one
 // value and the two orders of a pair agree bit for bit.
+// The partial sums run as two packed pairs (s0, s1) and (s2, s3) on the
+// paired float32 instructions of sm_100+ (sub.rn.f32x2, fma.rn.f32x2): each
+// lane of a pair is the IEEE round-to-nearest operation of the scalar form,
+// so the values are those of four scalar chains, with half the instructions.
+__device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f32x2_unpack(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
 struct Acc4 {
-    float s0, s1, s2, s3;
-    __device__ __forceinline__ Acc4() : s0(0.f), s1(0.f), s2(0.f), s3(0.f) {}
+    unsigned long long s01, s23;  // (s0, s1), (s2, s3)
+    __device__ __forceinline__ Acc4() : s01(0ull), s23(0ull) {}
     __device__ __forceinline__ void add(float4 a, float4 b) {
-        float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
-        s0 = fmaf(d0, d0, s0);
-        s1 = fmaf(d1, d1, s1);
-        s2 = fmaf(d2, d2, s2);
-        s3 = fmaf(d3, d3, s3);
+        unsigned long long d01, d23;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d01) : "l"(f32x2_pack(a.x, a.y)), "l"(f32x2_pack(b.x, b.y)));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d23) : "l"(f32x2_pack(a.z, a.w)), "l"(f32x2_pack(b.z, b.w)));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(s01) : "l"(d01));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(s23) : "l"(d23));
     }
-    __device__ __forceinline__ float sum() const { return (s0 + s1) + (s2 + s3); }
+    __device__ __forceinline__ float sum() const {
+        float s0, s1, s2, s3;
+        f32x2_unpack(s01, s0, s1);
+        f32x2_unpack(s23, s2, s3);
+        return (s0 + s1) + (s2 + s3);
+    }
 };
 
 __device__ __forceinline__ float l2sq_rows(const float4 *__restrict__ a, const float4 *__restrict__ b, int nv) {
@@ -194,7 +211,15 @@ struct DevState {
     const double *ds_thr;      // data set -> delta * n * K
     long long *ds_changes;     // data set x kMaxLocalIters change counts
     double thr;                // delta * n * K
+    // ring join path only (else null): per-node candidate sets written by the
+    // set kernel and read by the ring kernel
+    int *cset;                 // n x 64 candidate ids, new ones first
+    int *cmeta;                // n: ns | m << 8 (0: no join pair)
+    int join_path;             // JoinPath chosen for this context
 };
+
+// Which local-join kernel a context uses (fixed at creation).
+enum JoinPath : int { kJoinWarp = 0, kJoinTile = 1, kJoinRing = 2 };
 
 // Proposal buckets: run 0 of node p is inline (pbucket), runs 1..15 are pool
 // chunks claimed on demand with a CAS (a lane that loses the race uses the

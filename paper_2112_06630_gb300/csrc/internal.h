@@ -21,6 +21,18 @@ cudaError_t launch_sample(const DevState &st, int li, int it, uint64_t seed, cud
 cudaError_t launch_join(const DevState &st, int li, cudaStream_t s);
 cudaError_t launch_merge(const DevState &st, int li, cudaStream_t s);
 cudaError_t launch_tile_join(const DevState &st, int li, bool bf16, cudaStream_t s);
+cudaError_t launch_ring_join(const DevState &st, int li, cudaStream_t s);
+// true when a node with 64 candidates fits the ring of the ring join kernel
+bool ring_join_fits(int bf16, int nv, int dpb, int K);
+// true when the ring holds several typical nodes (the default choice)
+bool ring_join_preferred(int bf16, int nv, int dpb);
+// the join kernel for a context: the warp kernel for float32 rows of up to
+// 64 floats, else the ring kernel where a 64-candidate node fits its ring,
+// else the block-per-node tile kernel; `force` (>= 0) picks one a context can
+// run instead (test hook), -1 = default
+int choose_join_path(int bf16, int nv, int dpb, int K, int force);
+// kernel launches of one local join on the given path
+int join_launches(int path);
 cudaError_t launch_stage_bf16(const float *X, int64_t n, int dp, int d, uint16_t *Xb, int dpb, float *nrm,
                               cudaStream_t s);
 cudaError_t launch_greedy_reorder(const uint64_t *keys, int64_t n, int K, int reading_b, int32_t *sigma,

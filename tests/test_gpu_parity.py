@@ -132,6 +132,57 @@ def test_one_iteration_matches_oracle_bit_exact(n, d, K, rho, hi):
     assert stats["dist_evals"] == r["evals"]
 
 
+PATH_CASES = [
+    # n, d, K, rho, int range, bf16 flag
+    (4000, 600, 12, 0.5, 3, False),   # ~48 KB ring slots: every block wraps its ring
+    (700, 65, 32, 0.3, 4, False),     # 17 float4 per row, K = 32 list snapshots
+    (1500, 100, 20, 0.5, 3, False),
+    (1200, 64, 16, 0.5, 4, True),     # one 64-bf16 k-block
+    (600, 128, 32, 0.3, 4, True),
+    (2000, 150, 20, 1.0, 4, True),    # up to 64 candidates: four 16-row tiles
+]
+PATH_IDS = {"warp": 0, "tile": 1, "ring": 2}
+
+
+@pytest.mark.parametrize("path", ["tile", "ring"])
+@pytest.mark.parametrize("n,d,K,rho,hi,bf16", PATH_CASES)
+def test_join_kernels_match_oracle_bit_exact(path, n, d, K, rho, hi, bf16, monkeypatch):
+    """The block-per-node tile kernel and the TMA-staged ring kernel, forced
+    on the same inputs: one iteration bit-exact against the oracle (integer
+    data: the bf16 expansion is exact too)."""
+    monkeypatch.setenv("KNNG_TEST_JOIN_PATH", path)
+    x = _int_data(n, d, hi, seed=n + d)
+    ids0, new0 = workloads.random_graph(n, K, seed=n + 1, p_new=0.6)
+    flags = knng.FLAG_BF16 if bf16 else 0
+    with knng.Context(_cuda(x), K, rho=rho, seed=11, graph=(ids0, new0), iter=0, flags=flags) as c:
+        conv, ch = c.iterate()
+        gi, gd, gf = c.state()
+        stats = c.stats()
+    assert stats["join_path"] == PATH_IDS[path]
+    assert stats["set_overflow"] == 0 and stats["lock_timeouts"] == 0
+    st = oracle.State(x, K, rho, seed=11)
+    st.init_graph(ids0, new0, 0)
+    r = st.iterate()
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    assert ch == r["changes"]
+    assert stats["dist_evals"] == r["evals"]
+
+
+@pytest.mark.parametrize("path", ["warp", "tile", "ring"])
+def test_join_kernels_agree_on_real_valued_builds(path, monkeypatch):
+    """Whole float32 builds on real-valued clustered data through each join
+    kernel: every float32 distance uses the same arithmetic, so the three
+    kernels give the same graph bit for bit."""
+    monkeypatch.setenv("KNNG_TEST_JOIN_PATH", path)
+    x = workloads.gaussian_mixture(6000, 72, 20, seed=4)
+    ids, dists, st = knng.knng_build(_cuda(x), 16, 0.5, 0.001, 8, seed=2)
+    assert st["join_path"] == PATH_IDS[path]
+    monkeypatch.setenv("KNNG_TEST_JOIN_PATH", "warp")
+    ids_w, dists_w, _ = knng.knng_build(_cuda(x), 16, 0.5, 0.001, 8, seed=2)
+    assert torch.equal(ids, ids_w) and torch.equal(dists, dists_w)
+
+
 @pytest.mark.parametrize("pool", ["1", "40"])
 def test_bucket_overflow_paths_match_oracle_bit_exact(pool, monkeypatch):
     """A (test-only) tiny proposal pool forces runs past the first 256 keys of
@@ -145,6 +196,28 @@ def test_bucket_overflow_paths_match_oracle_bit_exact(pool, monkeypatch):
         conv, ch = c.iterate()
         gi, gd, gf = c.state()
         stats = c.stats()
+    st = oracle.State(x, K, rho, seed=11)
+    st.init_graph(ids0, new0, 0)
+    r = st.iterate()
+    assert stats["bucket_overflow"] > 0 and stats["lock_timeouts"] == 0
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    assert ch == r["changes"]
+
+
+@pytest.mark.parametrize("path", ["tile", "ring"])
+def test_bucket_overflow_paths_high_d_kernels(path, monkeypatch):
+    """The same tiny-pool overflow drive through the tile and ring kernels."""
+    monkeypatch.setenv("KNNG_TEST_BUCKET_POOL_CHUNKS", "1")
+    monkeypatch.setenv("KNNG_TEST_JOIN_PATH", path)
+    n, d, K, rho, hi = 1800, 70, 16, 0.5, 3
+    x = _int_data(n, d, hi, seed=n)
+    ids0, new0 = workloads.random_graph(n, K, seed=n + 1, p_new=0.6)
+    with knng.Context(_cuda(x), K, rho=rho, seed=11, graph=(ids0, new0), iter=0) as c:
+        conv, ch = c.iterate()
+        gi, gd, gf = c.state()
+        stats = c.stats()
+    assert stats["join_path"] == PATH_IDS[path]
     st = oracle.State(x, K, rho, seed=11)
     st.init_graph(ids0, new0, 0)
     r = st.iterate()
