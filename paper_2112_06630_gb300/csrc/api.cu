@@ -255,6 +255,13 @@ int ctx_alloc(knng_ctx *c) {
         c->cmeta = (int *)(a + oCm);
     }
     KNNG_TRY(cudaMemsetAsync(c->locks, 0, sizeof(int) * nint, c->stream));
+    // test hook: the locks of the first h lists start held, so a locked
+    // insertion into one of them runs its bounded wait out and the call
+    // reports KNNG_ERR_TIMEOUT
+    if (const char *e = std::getenv("KNNG_TEST_HOLD_LOCKS")) {
+        const int64_t h = std::min<int64_t>(n, std::max<int64_t>(1, std::atoll(e)));
+        KNNG_TRY(cudaMemsetAsync(c->locks, 1, sizeof(int) * h, c->stream));
+    }
     KNNG_TRY(cudaMemsetAsync(c->ibuf, 0, sizeof(int) * 6 * n, c->stream));
     KNNG_TRY(cudaMemsetAsync(c->stats, 0, sizeof(long long) * kStatCount, c->stream));
     KNNG_TRY(cudaMemsetAsync(c->it_stats, 0, sizeof(long long) * kItCount * kMaxLocalIters, c->stream));

@@ -21,9 +21,10 @@
 //     were measured at about 80 issuing cycles each).
 //   warps 1..15 (consumers) take nodes in order from a shared counter.  A
 //     consumer issues the copies of its next node (warp-wide 16-byte cp.async
-//     per row, the worst keys, bf16 norms) before it runs the current one,
-//     and never waits for a placement while it holds an unrun node.  The join
-//     of a node:
+//     per row, the worst keys, bf16 norms) as soon as the current node's rows
+//     are released, so they land while the current node's proposals go out;
+//     it never waits for a placement while it holds a node.  The join of a
+//     node:
 //       1. the distance block D[i][j] of new rows i against all rows j:
 //          float32: the canonical difference form (bit-identical to every
 //            other float32 distance in the library), register-blocked two
@@ -522,17 +523,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) ring_join_kernel(DevState st,
         ok = wait_placed(k_cur, nsm_cur);
         if (ok && nsm_cur) start(k_cur, nsm_cur);
         while (ok && nsm_cur) {
-            // claim the next node and start its copies if it is already placed
-            // (never block on a placement while holding an unprocessed node)
-            const int k_nxt = claim();
-            int nsm_nxt = 0;
-            const bool placed = mbar_test(&sh.full[k_nxt % kRingDesc], (k_nxt / kRingDesc) & 1);
-            if (placed) {
-                nsm_nxt = sh.desc[k_nxt % kRingDesc].nsm;
-                if (nsm_nxt) start(k_nxt, nsm_nxt);
-            }
-            if (placed && nsm_nxt) asm volatile("cp.async.wait_group 1;" ::: "memory");
-            else asm volatile("cp.async.wait_group 0;" ::: "memory");
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
             __syncwarp();
 
             const int s = k_cur % kRingDesc;
@@ -556,6 +547,16 @@ __global__ void __launch_bounds__(kRingThreads, 1) ring_join_kernel(DevState st,
             w_gathered += ns;
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh.empty_a[s]);  // the rows are no longer needed
+            // claim the next node and start its copies if it is already placed:
+            // they land while this node's proposals go out (a consumer never
+            // waits for a placement while it holds a node)
+            const int k_nxt = claim();
+            int nsm_nxt = 0;
+            const bool placed = mbar_test(&sh.full[k_nxt % kRingDesc], (k_nxt / kRingDesc) & 1);
+            if (placed) {
+                nsm_nxt = sh.desc[k_nxt % kRingDesc].nsm;
+                if (nsm_nxt) start(k_nxt, nsm_nxt);
+            }
             // ---- 2. proposals that order before the target's worst entry:
             //         element (i, j) of the block (i new) carries "j to i"
             //         (j != i) and, for an old j, "i to j" -- every proposal of
