@@ -834,10 +834,14 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
     cudaStream_t s = (cudaStream_t)stream;
     const int dp = (d + 3) & ~3;
     const size_t xb = align256(sizeof(float) * n * dp), rb = rows ? align256(sizeof(int64_t) * nq) : 0;
-    const size_t ib = align256(sizeof(int32_t) * nq * K), db = sizeof(float) * nq * K;
+    const size_t ib = align256(sizeof(int32_t) * nq * K), db = align256(sizeof(float) * nq * K);
     const bool dev_out = is_device_ptr(ids) && is_device_ptr(dists);
+    // slices of the point set when there are too few queries to fill the GPU
+    const int S = bruteforce_slices(n, nq);
+    const size_t pb = S > 1 ? sizeof(uint64_t) * (size_t)nq * S * K : 0;
     unsigned char *tmp = nullptr;
-    KNNG_TRY(lib_malloc((void **)&tmp, xb + rb + (dev_out ? 0 : ib + db), s));
+    KNNG_TRY(lib_malloc((void **)&tmp, xb + rb + (dev_out ? 0 : ib + db) + pb, s));
+    uint64_t *part = S > 1 ? (uint64_t *)(tmp + xb + rb + (dev_out ? 0 : ib + db)) : nullptr;
     float *X = (float *)tmp;
     int rc = KNNG_OK;
     const float *src = data;
@@ -863,10 +867,10 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
         oi = (int32_t *)(tmp + xb + rb);
         od = (float *)(tmp + xb + rb + ib);
     }
-    if (e == cudaSuccess) e = launch_bruteforce(X, n, dp, K, rows_d, nq, oi, od, s);
+    if (e == cudaSuccess) e = launch_bruteforce(X, n, dp, K, rows_d, nq, oi, od, s, part, S);
     if (e == cudaSuccess && !dev_out) {
         e = cudaMemcpyAsync(ids, oi, sizeof(int32_t) * nq * K, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dists, od, db, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dists, od, sizeof(float) * nq * K, cudaMemcpyDeviceToHost, s);
     }
     if (staged) cudaFreeAsync(staged, s);
     cudaFreeAsync(tmp, s);

@@ -1,12 +1,16 @@
 // bruteforce.cu -- exact K-NNG (Section 2: every distance, the K smallest per
 // point), the ground truth that recall is measured against.
 //
-// A block of 128 threads takes 128 query points; all points stream through
-// shared memory in tiles that every thread reads by broadcast.  Each thread
-// keeps its query's best K keys (dist, id) sorted in registers and inserts a
-// candidate only when it beats the current K-th key.  Distances use the
-// library's canonical float32 difference form, so ground truth and NN-Descent
-// agree on the value of every pair.
+// A block of 128 threads takes 128 query points and one slice of the points;
+// the slice streams through shared memory in tiles that every thread reads by
+// broadcast.  Each thread keeps its query's best K keys (dist, id) sorted in
+// registers and inserts a candidate only when it beats the current K-th key.
+// With few queries the points are cut into S slices (a second grid
+// dimension) so that every SM has work; each slice's sorted list goes to
+// scratch and one warp per query merges the S lists (bitonic merges of 32
+// keys).  Distances use the library's canonical float32 difference form, so
+// ground truth and NN-Descent agree on the value of every pair.
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/knng.h"
@@ -32,7 +36,8 @@ template <int KMAX, int NVR>
 __global__ void __launch_bounds__(kBfThreads) bruteforce_kernel(const float4 *__restrict__ X4, int64_t n, int nv,
                                                                 int K, const int64_t *__restrict__ rows,
                                                                 int64_t nq, int32_t *__restrict__ ids,
-                                                                float *__restrict__ dists, int tile) {
+                                                                float *__restrict__ dists, int tile,
+                                                                uint64_t *__restrict__ part, int64_t chunk) {
     extern __shared__ __align__(16) float4 tile_s[];
     const int64_t q = (int64_t)blockIdx.x * kBfThreads + threadIdx.x;
     const bool live = q < nq;
@@ -51,8 +56,9 @@ __global__ void __launch_bounds__(kBfThreads) bruteforce_kernel(const float4 *__
     uint64_t L[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) L[k] = k >= off ? kKeyEmpty : 0ull;
-    for (int64_t t0 = 0; t0 < n; t0 += tile) {
-        const int cnt = (int)min((int64_t)tile, n - t0);
+    const int64_t p0 = (int64_t)blockIdx.y * chunk, p1 = min(n, p0 + chunk);
+    for (int64_t t0 = p0; t0 < p1; t0 += tile) {
+        const int cnt = (int)min((int64_t)tile, p1 - t0);
         __syncthreads();
         for (int e = threadIdx.x; e < cnt * nv; e += kBfThreads) tile_s[e] = X4[(size_t)t0 * nv + e];
         __syncthreads();
@@ -73,7 +79,13 @@ __global__ void __launch_bounds__(kBfThreads) bruteforce_kernel(const float4 *__
             }
         }
     }
-    if (live) {
+    if (live && part) {
+        // this slice's sorted list (empty slots stay all ones)
+        uint64_t *dst = part + ((size_t)q * gridDim.y + blockIdx.y) * K;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k >= off) dst[k - off] = L[k];
+    } else if (live) {
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
             if (k >= off) {
@@ -84,10 +96,41 @@ __global__ void __launch_bounds__(kBfThreads) bruteforce_kernel(const float4 *__
     }
 }
 
+// One warp per query merges its S sorted slice lists of K keys: the running
+// list A (ascending, lane k = entry k) and the next list B read in reverse
+// give min(A[l], B[31 - l]), a bitonic sequence holding the 32 smallest keys
+// of both, which five compare-exchange stages sort ascending.  A point lies in
+// one slice only, so no key repeats.
+__global__ void __launch_bounds__(256) bruteforce_merge_kernel(const uint64_t *__restrict__ part, int S, int K,
+                                                               int64_t nq, int32_t *__restrict__ ids,
+                                                               float *__restrict__ dists) {
+    const unsigned lane = lane_id();
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq;
+         q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const uint64_t *P = part + (size_t)q * S * K;
+        uint64_t A = (int)lane < K ? P[lane] : kKeyEmpty;
+        for (int y = 1; y < S; ++y) {
+            const int r = 31 - (int)lane;
+            const uint64_t B = r < K ? P[(size_t)y * K + r] : kKeyEmpty;
+            uint64_t C = A < B ? A : B;
+#pragma unroll
+            for (int j = 16; j > 0; j >>= 1) {
+                const uint64_t o = shfl_xor_u64(C, j);
+                C = (lane & j) ? (C > o ? C : o) : (C < o ? C : o);
+            }
+            A = C;
+        }
+        if ((int)lane < K) {
+            ids[(size_t)q * K + lane] = (int32_t)key_id(A);
+            dists[(size_t)q * K + lane] = key_dist(A);
+        }
+    }
+}
+
 namespace {
 template <int KMAX, int NVR>
 cudaError_t launch_bf_t(const float *X, int64_t n, int nv, int K, const int64_t *rows, int64_t nq, int32_t *ids,
-                        float *dists, cudaStream_t s) {
+                        float *dists, cudaStream_t s, uint64_t *part, int S) {
     int tile = (int)(kBfSmem / ((size_t)nv * 16));
     if (tile > 256) tile = 256;
     if (tile < 1) tile = 1;
@@ -96,28 +139,45 @@ cudaError_t launch_bf_t(const float *X, int64_t n, int nv, int K, const int64_t 
     cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (nq + kBfThreads - 1) / kBfThreads;
-    kern<<<(unsigned)blocks, kBfThreads, dyn, s>>>(reinterpret_cast<const float4 *>(X), n, nv, K, rows, nq, ids,
-                                                  dists, tile);
+    const int64_t chunk = (n + S - 1) / S;
+    kern<<<dim3((unsigned)blocks, (unsigned)S), kBfThreads, dyn, s>>>(reinterpret_cast<const float4 *>(X), n, nv, K,
+                                                                     rows, nq, ids, dists, tile,
+                                                                     S > 1 ? part : nullptr, chunk);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || S == 1) return e;
+    const int mgrid = grid_for((const void *)bruteforce_merge_kernel, 256, 0);
+    bruteforce_merge_kernel<<<mgrid, 256, 0, s>>>(part, S, K, nq, ids, dists);
     return cudaGetLastError();
 }
 
 template <int KMAX>
 cudaError_t launch_bf_k(const float *X, int64_t n, int nv, int K, const int64_t *rows, int64_t nq, int32_t *ids,
-                        float *dists, cudaStream_t s) {
-    if (nv == 2) return launch_bf_t<KMAX, 2>(X, n, nv, K, rows, nq, ids, dists, s);
-    if (nv == 4) return launch_bf_t<KMAX, 4>(X, n, nv, K, rows, nq, ids, dists, s);
-    if (nv == 8) return launch_bf_t<KMAX, 8>(X, n, nv, K, rows, nq, ids, dists, s);
-    return launch_bf_t<KMAX, 0>(X, n, nv, K, rows, nq, ids, dists, s);
+                        float *dists, cudaStream_t s, uint64_t *part, int S) {
+    if (nv == 2) return launch_bf_t<KMAX, 2>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
+    if (nv == 4) return launch_bf_t<KMAX, 4>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
+    if (nv == 8) return launch_bf_t<KMAX, 8>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
+    return launch_bf_t<KMAX, 0>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
 }
 }  // namespace
 
+int bruteforce_slices(int64_t n, int64_t nq) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t qblocks = (nq + kBfThreads - 1) / kBfThreads, want = 4LL * sms;
+    int64_t S = (want + qblocks - 1) / qblocks;
+    S = std::min<int64_t>(S, std::max<int64_t>(1, n / 4096));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(S, 256));
+}
+
 cudaError_t launch_bruteforce(const float *X, int64_t n, int dp, int K, const int64_t *rows, int64_t nq,
-                              int32_t *ids, float *dists, cudaStream_t s) {
+                              int32_t *ids, float *dists, cudaStream_t s, uint64_t *part, int S) {
     const int nv = dp / 4;
-    if (K <= 8) return launch_bf_k<8>(X, n, nv, K, rows, nq, ids, dists, s);
-    if (K <= 16) return launch_bf_k<16>(X, n, nv, K, rows, nq, ids, dists, s);
-    if (K <= 24) return launch_bf_k<24>(X, n, nv, K, rows, nq, ids, dists, s);
-    return launch_bf_k<32>(X, n, nv, K, rows, nq, ids, dists, s);
+    if (!part) S = 1;
+    if (K <= 8) return launch_bf_k<8>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
+    if (K <= 16) return launch_bf_k<16>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
+    if (K <= 24) return launch_bf_k<24>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
+    return launch_bf_k<32>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
 }
 
 }  // namespace knng
@@ -183,6 +243,6 @@ extern "C" int knng_bruteforce_noalloc(const float *data, int64_t n, int d, int 
     // staging writes every element of the n x dp region it uses (padding
     // included), so nothing left by an earlier call is read
     e = knng::launch_stage(data, n, d, X, dp, s);
-    if (e == cudaSuccess) e = knng::launch_bruteforce(X, n, dp, K, rows, nq, ids, dists, s);
+    if (e == cudaSuccess) e = knng::launch_bruteforce(X, n, dp, K, rows, nq, ids, dists, s, nullptr, 1);
     return e == cudaSuccess ? KNNG_OK : KNNG_ERR_CUDA;
 }

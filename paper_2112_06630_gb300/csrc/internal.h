@@ -44,7 +44,11 @@ cudaError_t launch_output(const DevState &st, const int32_t *total_perm, const i
 cudaError_t launch_iota(int32_t *p, int64_t n, cudaStream_t s);
 cudaError_t launch_ds_map(const long long *ds_off, int nds, int64_t n, int *ds, cudaStream_t s);
 cudaError_t launch_invert(const int32_t *perm, int64_t n, int32_t *inv, cudaStream_t s);
+// part: scratch for S slice lists of K keys per query (nq * S * K uint64), or
+// null for one slice (no scratch)
 cudaError_t launch_bruteforce(const float *X, int64_t n, int dp, int K, const int64_t *rows, int64_t nq,
-                              int32_t *ids, float *dists, cudaStream_t s);
+                              int32_t *ids, float *dists, cudaStream_t s, uint64_t *part, int S);
+// slices that give every SM work for nq queries over n points
+int bruteforce_slices(int64_t n, int64_t nq);
 
 }  // namespace knng
