@@ -37,7 +37,7 @@ namespace knng {
 namespace {
 constexpr int kJoinWarps = 4;
 constexpr int kMergeWarps = 8;
-constexpr int kTileMinNv = 16;  // rows longer than 64 floats go to the tile kernel
+constexpr int kWarpMaxNv = 8;   // float32 rows of up to 32 floats take the warp kernel (measured crossover)
 constexpr int kSortMergeMin = 6; // candidates per 32-key batch from which a sort-merge beats insertions
 
 struct JoinLayout {
@@ -412,7 +412,7 @@ int choose_join_path(int bf16, int nv, int dpb, int K, int force) {
     if (force == kJoinWarp && !bf16) return kJoinWarp;
     if (force == kJoinTile) return kJoinTile;
     if (force == kJoinRing && ring) return kJoinRing;
-    if (!bf16 && nv <= kTileMinNv) return kJoinWarp;
+    if (!bf16 && nv <= kWarpMaxNv) return kJoinWarp;
     return ring && ring_join_preferred(bf16, nv, dpb) ? kJoinRing : kJoinTile;
 }
 
