@@ -15,18 +15,19 @@
 //      every unordered pair exactly once) and new(u) x old(u) as a rectangle --
 //      with all 32 lanes taking consecutive pairs.  A pair whose key beats the
 //      snapshot worst of an endpoint sets the partner's bit in that endpoint's
-//      64-bit proposal mask (shared-memory atomicOr);
-//   4. lane per target with proposals: one atomicAdd reserves a run in the
+//      proposal mask (two 32-bit words, shared-memory atomicOr);
+//   4. lane per target with proposals: one atomicAdd reserves a range of the
 //      target's proposal bucket and the lane writes the keys (recomputing each
-//      pair with the same arithmetic, so the same bits).  A bucket that is
-//      full takes the rest by a locked insertion into the list (bounded spin;
-//      rare).  A bucket is a 256-key run per node plus up to 15 runs claimed
-//      from a pool on demand, so hub nodes hold up to 4,096 proposals.
+//      pair with the same arithmetic, so the same bits).  A proposal whose run
+//      has no slot (bucket full or pool spent) is marked and then inserted
+//      into the list under the list's lock (bounded spin; rare).  A
+//      bucket is a 256-key run per node plus up to 15 runs claimed from a pool
+//      on demand, so hub nodes hold up to 4,096 proposals.
 // merge_kernel: one warp per node with a non-empty bucket: lane k holds list
-//   entry k; bucket keys arrive 32 at a time, those beating the worst are
-//   inserted one by one with ballots (skip if the id is listed).  The entries
-//   still flagged "inserted in this iteration" at the end are the iteration's
-//   changes for that list.
+//   entry k; bucket keys arrive 32 at a time, those that order before the
+//   worst and are not listed go in (a sort-merge for six or more, else one by
+//   one with ballots).  The entries still flagged "inserted in this
+//   iteration" at the end are the iteration's changes for that list.
 // Since every float32 distance in the library uses the same arithmetic, a pair
 // always yields the same key, and each list ends as the K smallest distinct
 // keys of its start entries and all proposals it received, whatever the order.
@@ -35,6 +36,14 @@
 namespace knng {
 
 namespace {
+__device__ __forceinline__ void cp_async16_w(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8_w(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
 constexpr int kJoinWarps = 4;
 constexpr int kMergeWarps = 8;
 constexpr int kWarpMaxNv = 8;   // float32 rows of up to 32 floats take the warp kernel (measured crossover)
@@ -48,9 +57,10 @@ struct JoinLayout {
     size_t per_warp;  // bytes
 };
 
-// per-warp shared memory: sid[64] | base[64] | swk[64] | mask[64] | scratch
+// per-warp shared memory: sid[64] | (spare)[64] | swk[64] | mask[64] | scratch,
 // where scratch holds the raw candidate ids and the hash set until repeats
-// are removed, and the staged rows[64][rs] afterwards
+// are removed, and the staged rows[64][rs] afterwards; swk becomes the
+// per-target mask of proposals that found no bucket slot
 __host__ __device__ inline JoinLayout join_layout(int cap, int nv, bool rows_smem) {
     JoinLayout L;
     L.raw_max = ((2 * cap + 31) / 32) * 32;
@@ -82,9 +92,9 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
     const JoinLayout lay = join_layout(cap, nv, kRowsSmem);
     unsigned char *wbase = smem + (size_t)warp * lay.per_warp;
     int *sid = reinterpret_cast<int *>(wbase);
-    int *base = sid + kSetMax;
     uint64_t *swk = reinterpret_cast<uint64_t *>(wbase + lay.off_swk);
     unsigned long long *mask = reinterpret_cast<unsigned long long *>(swk + kSetMax);
+    unsigned *mw = reinterpret_cast<unsigned *>(mask);  // the masks as 32-bit words (native shared atomics)
     float4 *rows = reinterpret_cast<float4 *>(wbase + lay.off_rows);
     int *hset = reinterpret_cast<int *>(wbase + lay.off_rows);  // aliases rows until they are staged
     int *raw = hset + (1 << kHashBits);
@@ -104,17 +114,19 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
         if (ns == 0) continue;  // no new candidate: no join pair
         const int o = ns - m;
         __syncwarp();
-        // ---- 2. snapshot worst keys, clear masks, stage rows
+        // ---- 2. snapshot worst keys, clear masks, stage rows (asynchronous
+        //         copies: one round trip for all of them)
         for (int i = lane; i < ns; i += 32) {
-            swk[i] = __ldcg(st.keys + (size_t)sid[i] * K + (K - 1));
+            cp_async8_w(swk + i, st.keys + (size_t)sid[i] * K + (K - 1));
             mask[i] = 0ull;
         }
         if (kRowsSmem) {
             for (int idx = lane; idx < ns * nv; idx += 32) {
                 const int r = idx / nv, c = idx - r * nv;
-                rows[r * rs + c] = __ldg(X4 + (size_t)sid[r] * nv + c);
+                cp_async16_w(rows + r * rs + c, X4 + (size_t)sid[r] * nv + c);
             }
         }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
         __syncwarp();
         w_gathered += ns;
         // ---- 3. every join pair once, all lanes busy
@@ -141,14 +153,19 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
             const float4 *ri = kRowsSmem ? rows + i * rs : X4 + (size_t)sid[i] * nv;
             const float4 *rj = kRowsSmem ? rows + j * rs : X4 + (size_t)sid[j] * nv;
             const float dd = l2sq_rows(ri, rj, nv);
-            if (make_key(dd, (uint32_t)sid[j], kFlagNew | kFlagIns) < swk[i]) atomicOr(&mask[i], 1ull << j);
-            if (make_key(dd, (uint32_t)sid[i], kFlagNew | kFlagIns) < swk[j]) atomicOr(&mask[j], 1ull << i);
+            if (make_key(dd, (uint32_t)sid[j], kFlagNew | kFlagIns) < swk[i])
+                atomicOr(&mw[2 * i + (j >> 5)], 1u << (j & 31));
+            if (make_key(dd, (uint32_t)sid[i], kFlagNew | kFlagIns) < swk[j])
+                atomicOr(&mw[2 * j + (i >> 5)], 1u << (i & 31));
         }
         __syncwarp();
         // ---- 4. bucket runs: lane = target; one reservation per target, then
-        //         the lane writes its run (recomputing each pair with the
-        //         arithmetic of step 3, so the keys are bit-identical)
-        unsigned ovf_lo = 0, ovf_hi = 0;  // targets whose run did not fit
+        //         the lane writes its run (each key recomputed with the
+        //         arithmetic of step 3, so it is bit-identical); a proposal
+        //         whose run has no slot (bucket or pool spent) is marked for
+        //         the locked insertion
+        unsigned long long *fails = reinterpret_cast<unsigned long long *>(swk);  // swk is done
+        unsigned ovf_lo = 0, ovf_hi = 0;  // targets with marked proposals
         for (int t = lane; t < ns; t += 32) {
             const unsigned long long mt = mask[t];
             const int c = __popcll(mt);
@@ -170,7 +187,22 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
                 *slot = make_key(l2sq_rows(rt, rj, nv), (uint32_t)sid[j], kFlagNew | kFlagIns);
             }
             if (fit < c) {
-                base[t] = fit;  // proposals of t from rank `fit` on still to insert
+                // rare: a run without a slot; later runs of this range may
+                // still have one (claimed by another warp), and every slot of
+                // a valid run must be written -- mark only the proposals whose
+                // run has none
+                unsigned long long failed = 0ull;
+                for (; fit < c; ++fit, mm &= mm - 1) {
+                    const int j = __ffsll((long long)mm) - 1;
+                    uint64_t *d = bucket_slot(st, p, b + fit);
+                    if (d) {
+                        const float4 *rj = kRowsSmem ? rows + j * rs : X4 + (size_t)sid[j] * nv;
+                        *d = make_key(l2sq_rows(rt, rj, nv), (uint32_t)sid[j], kFlagNew | kFlagIns);
+                    } else {
+                        failed |= 1ull << j;
+                    }
+                }
+                fails[t] = failed;
                 if (t < 32) ovf_lo |= 1u << t;
                 else ovf_hi |= 1u << (t - 32);
             }
@@ -178,14 +210,12 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
         ovf_lo = __reduce_or_sync(kFull, ovf_lo);
         ovf_hi = __reduce_or_sync(kFull, ovf_hi);
         __syncwarp();
-        // full buckets (rare): insert the rest straight into the list, locked
+        // full buckets (rare): insert those proposals straight into the list, locked
         for (unsigned long long om = (unsigned long long)ovf_lo | ((unsigned long long)ovf_hi << 32); om;
              om &= om - 1) {
             const int t = __ffsll((long long)om) - 1;
             const uint32_t p = (uint32_t)sid[t];
-            // partner bits of t from rank base[t] on
-            unsigned long long rest = mask[t];
-            for (int r = 0; r < base[t]; ++r) rest &= rest - 1;
+            const unsigned long long rest = fails[t];
             w_ovf += __popcll(rest);
             const float4 *rt = kRowsSmem ? rows + t * rs : X4 + (size_t)p * nv;
             uint64_t xs[2];

@@ -81,7 +81,7 @@ __host__ __device__ __forceinline__ Geometry geometry(int bf16, int nv, int dpb)
 __host__ __device__ __forceinline__ uint32_t slot_a_bytes(int ns, const Geometry &g) {
     return align_up((uint32_t)ns * g.stride, 128);
 }
-// ring B: ids | worst keys | masks | norms | overflow ranks | distance block
+// ring B: ids | worst keys | masks | norms | failed-proposal masks | distance block
 // (m rows of stride ns | 1 floats)
 struct SlotB {
     uint32_t o_swk, o_mask, o_nrm, o_ovf, o_D, size;
@@ -92,7 +92,7 @@ __host__ __device__ __forceinline__ SlotB slot_b(int ns, int m) {
     L.o_mask = align_up(L.o_swk + 8u * ns, 16);
     L.o_nrm = align_up(L.o_mask + 8u * ns, 16);
     L.o_ovf = align_up(L.o_nrm + 4u * ns, 16);
-    L.o_D = align_up(L.o_ovf + 4u * ns, 16);
+    L.o_D = align_up(L.o_ovf + 8u * ns, 16);
     L.size = align_up(L.o_D + 4u * (uint32_t)m * (uint32_t)(ns | 1), 128);
     return L;
 }
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) ring_join_kernel(DevState st,
             unsigned *mw = reinterpret_cast<unsigned *>(sb + LB.o_mask);  // two 32-bit words per target
             unsigned long long *mask = reinterpret_cast<unsigned long long *>(sb + LB.o_mask);
             const float *nrm = reinterpret_cast<const float *>(sb + LB.o_nrm);
-            int *ovf_from = reinterpret_cast<int *>(sb + LB.o_ovf);
+            unsigned long long *fails = reinterpret_cast<unsigned long long *>(sb + LB.o_ovf);
             float *D = reinterpret_cast<float *>(sb + LB.o_D);
             const int ds = ns | 1;
             for (int i = lane; i < 2 * ns; i += 32) mw[i] = 0u;
@@ -586,20 +586,21 @@ __global__ void __launch_bounds__(kRingThreads, 1) ring_join_kernel(DevState st,
                 l_props += c;
                 const uint32_t p = (uint32_t)sid[t];
                 const int b = atomicAdd(st.pcursor + p, c);
-                unsigned long long mm = mt;
-                int fit = 0;
+                // a proposal whose run has no slot (bucket or pool spent) is
+                // marked for the locked insertion; the others are written
+                unsigned long long mm = mt, failed = 0ull;
                 uint64_t *dst = nullptr;
-                for (; fit < c; ++fit, mm &= mm - 1) {
-                    const int pos = b + fit;
-                    if (fit == 0 || (pos & (kBucketRun - 1)) == 0) dst = bucket_slot(st, p, pos);
-                    else ++dst;
-                    if (!dst) break;
+                for (int r = 0; r < c; ++r, mm &= mm - 1) {
+                    const int pos = b + r;
+                    if (r == 0 || (pos & (kBucketRun - 1)) == 0) dst = bucket_slot(st, p, pos);
+                    else if (dst) ++dst;
                     const int j = __ffsll((long long)mm) - 1;
                     const float dd = t < m ? D[t * ds + j] : D[j * ds + t];
-                    *dst = make_key(dd, (uint32_t)sid[j], kFlagNew | kFlagIns);
+                    if (dst) *dst = make_key(dd, (uint32_t)sid[j], kFlagNew | kFlagIns);
+                    else failed |= 1ull << j;
                 }
-                if (fit < c) {
-                    ovf_from[t] = fit;
+                fails[t] = failed;
+                if (failed) {
                     if (t < 32) ovf_lo |= 1u << t;
                     else ovf_hi |= 1u << (t - 32);
                 }
@@ -611,8 +612,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) ring_join_kernel(DevState st,
             for (unsigned long long om = (unsigned long long)ovf_lo | ((unsigned long long)ovf_hi << 32); om;
                  om &= om - 1) {
                 const int t = __ffsll((long long)om) - 1;
-                unsigned long long rest = mask[t];
-                for (int r = 0; r < ovf_from[t]; ++r) rest &= rest - 1;
+                const unsigned long long rest = fails[t];
                 w_ovf += __popcll(rest);
                 uint64_t xs[2];
 #pragma unroll

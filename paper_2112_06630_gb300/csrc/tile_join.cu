@@ -49,7 +49,7 @@ struct TileSmem {
     float nrm[kSetMax];
     float D[kSetMax * kDStride];
     unsigned long long ovf;
-    int ovf_from[kSetMax];
+    unsigned long long fails[kSetMax];  // proposals that found no bucket slot, per target
     int ns, m;
     long long stat[8];
 };
@@ -315,30 +315,28 @@ __global__ void __launch_bounds__(kTileThreads) tile_join_kernel(DevState st, in
                 t_props += c;
                 const uint32_t p = (uint32_t)sm.sid[t];
                 const int b = atomicAdd(st.pcursor + p, c);
-                unsigned long long mm = mt;
-                int fit = 0;
+                // a proposal whose run has no slot (bucket or pool spent) is
+                // marked for the locked insertion; the others are written
+                unsigned long long mm = mt, failed = 0ull;
                 uint64_t *slot = nullptr;
-                for (; fit < c; ++fit, mm &= mm - 1) {
-                    const int pos = b + fit;
-                    if (fit == 0 || (pos & (kBucketRun - 1)) == 0) slot = bucket_slot(st, p, pos);
-                    else ++slot;
-                    if (!slot) break;
+                for (int r = 0; r < c; ++r, mm &= mm - 1) {
+                    const int pos = b + r;
+                    if (r == 0 || (pos & (kBucketRun - 1)) == 0) slot = bucket_slot(st, p, pos);
+                    else if (slot) ++slot;
                     const int j = __ffsll((long long)mm) - 1;
                     const float dd = t < m ? sm.D[t * kDStride + j] : sm.D[j * kDStride + t];
-                    *slot = make_key(dd, (uint32_t)sm.sid[j], kFlagNew | kFlagIns);
+                    if (slot) *slot = make_key(dd, (uint32_t)sm.sid[j], kFlagNew | kFlagIns);
+                    else failed |= 1ull << j;
                 }
-                if (fit < c) {
-                    sm.ovf_from[t] = fit;
-                    atomicOr(&sm.ovf, 1ull << t);
-                }
+                sm.fails[t] = failed;
+                if (failed) atomicOr(&sm.ovf, 1ull << t);
             }
             __syncthreads();
             // ---- 7. full buckets (rare): locked insertion, warp 0
             if (warp == 0) {
                 for (unsigned long long om = sm.ovf; om; om &= om - 1) {
                     const int t = __ffsll((long long)om) - 1;
-                    unsigned long long rest = sm.mask[t];
-                    for (int r = 0; r < sm.ovf_from[t]; ++r) rest &= rest - 1;
+                    const unsigned long long rest = sm.fails[t];
                     if (lane == 0) t_ovf += __popcll(rest);
                     uint64_t xs[2];
 #pragma unroll
