@@ -311,8 +311,43 @@ __device__ __forceinline__ int warp_sort_merge(uint64_t &Lk, uint64_t x, int K, 
     return __popc(__ballot_sync(kFull, valid && rank_c < K));
 }
 
-// One warp per node with proposals: merge its bucket into its list.
-__global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(DevState st, int li) {
+// One batch of up to 32 bucket keys (one per lane, kKeyEmpty = none) into
+// the list held one entry per lane.  Keys that cannot enter are dropped in
+// parallel: not before the worst, or already listed (a pair has one key, so
+// "listed" is "the same (dist, id) at its lower bound", a binary search over
+// the lanes; bf16 keys of a pair may differ from its float32 key in the list,
+// so there the id is looked up).  Returns the number of insertions.
+__device__ __forceinline__ int merge_batch(uint64_t &Lk, uint64_t x, int K, bool bf16, uint64_t *scratch) {
+    const uint64_t xo = key_order(x);
+    int lo = 0, hi = K - 1;
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int mid = (lo + hi) >> 1;
+        const uint64_t lm = __shfl_sync(kFull, Lk, mid);
+        if (lo < hi) {
+            if (key_order(lm) < xo) lo = mid + 1;
+            else hi = mid;
+        }
+    }
+    bool listed = key_order(__shfl_sync(kFull, Lk, lo)) == xo;
+    if (bf16) {
+        const uint32_t xi = key_id(x);
+        for (int k = 0; k < K; ++k) listed |= key_id(__shfl_sync(kFull, Lk, k)) == xi;
+    }
+    unsigned cand = __ballot_sync(kFull, x < __shfl_sync(kFull, Lk, K - 1) && !listed);
+    int ins = 0;
+    if (__popc(cand) >= kSortMergeMin) {
+        ins += warp_sort_merge(Lk, ((cand >> lane_id()) & 1u) ? x : kKeyEmpty, K, scratch);
+    } else {
+        for (; cand; cand &= cand - 1) ins += warp_insert(Lk, __shfl_sync(kFull, x, __ffs(cand) - 1), K);
+    }
+    return ins;
+}
+
+// One warp per node with proposals: merge its bucket into its list.  The
+// bucket's inline run (up to 256 keys) is loaded two batches ahead of the
+// merges; pool runs (hub nodes) stream batch by batch.
+__global__ void __launch_bounds__(kMergeWarps * 32, 4) merge_kernel(DevState st, int li) {
     if (iteration_skipped(st, li)) return;
     __shared__ uint64_t scratch_all[kMergeWarps][kMaxK];
     uint64_t *scratch = scratch_all[threadIdx.x >> 5];
@@ -337,11 +372,22 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(DevState st, in
         int *chunks = st.pchunk + (size_t)p * kBucketChunks;
         uint64_t Lk = valid ? row[lane] : kKeyEmpty;
         int ins = 0;
+        const bool bf16 = st.bf16 != 0;
+        // the inline run, its loads two batches ahead of the merges
         const uint64_t *run = st.pbucket + ((size_t)p << kBucketRunBits);
-        for (int c0 = 0; c0 < cnt; c0 += 32) {
-            // runs are multiples of 32 keys: a batch of 32 never straddles two
+        const int c_in = min(cnt, kBucketRun);
+        uint64_t x0 = (int)lane < c_in ? __ldcs(run + lane) : kKeyEmpty;
+        uint64_t x1 = 32 + (int)lane < c_in ? __ldcs(run + 32 + lane) : kKeyEmpty;
+        for (int c0 = 0; c0 < c_in; c0 += 32) {
+            const uint64_t x = x0;
+            x0 = x1;
+            x1 = c0 + 64 + (int)lane < c_in ? __ldcs(run + c0 + 64 + lane) : kKeyEmpty;
+            ins += merge_batch(Lk, x, K, bf16, scratch);
+        }
+        // pool runs (runs are multiples of 32 keys: a batch never straddles two)
+        for (int c0 = kBucketRun; c0 < cnt; c0 += 32) {
             const int k = c0 >> kBucketRunBits;
-            if (k > 0 && (c0 & (kBucketRun - 1)) == 0) {
+            if ((c0 & (kBucketRun - 1)) == 0) {
                 const int ch = chunks[k - 1];
                 __syncwarp();
                 if (lane == 0) chunks[k - 1] = 0;
@@ -351,33 +397,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(DevState st, in
             if (!run) continue;
             const int off = c0 & (kBucketRun - 1);
             const uint64_t x = c0 + (int)lane < cnt ? __ldcs(run + off + lane) : kKeyEmpty;
-            // drop, in parallel, keys that cannot enter: not before the worst,
-            // or already listed (a pair has one key, so "listed" is "the same
-            // (dist, id) at its lower bound"; binary search over the lanes)
-            const uint64_t xo = key_order(x);
-            int lo = 0, hi = K - 1;
-#pragma unroll
-            for (int step = 0; step < 5; ++step) {
-                const int mid = (lo + hi) >> 1;
-                const uint64_t lm = __shfl_sync(kFull, Lk, mid);
-                if (lo < hi) {
-                    if (key_order(lm) < xo) lo = mid + 1;
-                    else hi = mid;
-                }
-            }
-            bool listed = key_order(__shfl_sync(kFull, Lk, lo)) == xo;
-            if (st.bf16) {
-                // bf16 keys of a pair may differ from its float32 key in the
-                // list: look the id up
-                const uint32_t xi = key_id(x);
-                for (int k = 0; k < K; ++k) listed |= key_id(__shfl_sync(kFull, Lk, k)) == xi;
-            }
-            unsigned cand = __ballot_sync(kFull, x < __shfl_sync(kFull, Lk, K - 1) && !listed);
-            if (__popc(cand) >= kSortMergeMin) {
-                ins += warp_sort_merge(Lk, ((cand >> lane) & 1u) ? x : kKeyEmpty, K, scratch);
-            } else {
-                for (; cand; cand &= cand - 1) ins += warp_insert(Lk, __shfl_sync(kFull, x, __ffs(cand) - 1), K);
-            }
+            ins += merge_batch(Lk, x, K, bf16, scratch);
         }
         // entries flagged "inserted in this iteration" that are still listed
         // (the sampling pass cleared that flag everywhere before the join)
