@@ -196,12 +196,15 @@ typedef struct knng_desc {
 
 /*
  * K-NNGs of many independent data sets in one run (each as knng_build with
- * the same K, rho, delta, max_iters, seed and flags): the data sets share one
- * node space, so every step of every iteration is one kernel launch for all
- * of them.  Data sets of different d are zero-padded to the widest (this
- * leaves every distance unchanged); each stops on its own change count
+ * the same K, rho, delta, max_iters, seed and flags).  The data sets are
+ * grouped by row-width class (d up to 32, 48, 64, 96, 128, 192, 256, ...,
+ * each class 4/3 or 3/2 of the one before); the data sets of a class share
+ * one node space, so every step of every iteration is one kernel launch for
+ * all of them, and their rows are zero-padded to the class width (this leaves
+ * every distance unchanged).  Each data set stops on its own change count
  * (delta * n_b * K), and the random streams are keyed by ids local to the data
  * set, so each result equals what knng_build_ex gives for that data set alone.
+ * stats (may be NULL) sums the counters of all classes.
  * Requires 2 <= n_b, K <= n_b - 1 for every data set and a total below 2^30
  * nodes; KNNG_FLAG_REORDER is not supported here (KNNG_ERR_UNSUPPORTED).
  * Returns when all outputs are written.

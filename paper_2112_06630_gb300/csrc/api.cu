@@ -724,10 +724,13 @@ int knng_build(const float *data, int64_t n, int d, int K, float rho, float delt
     return knng_build_ex(data, n, d, K, rho, delta, max_iters, seed, 0u, nullptr, ids, dists, nullptr);
 }
 
-int knng_build_batched(const knng_desc *descs, int count, int K, float rho, float delta, int max_iters,
-                       uint64_t seed, uint32_t flags, void *stream, knng_stats *stats) {
-    if (!descs || count < 1 || max_iters < 0 || max_iters > kMaxItersArg) return KNNG_ERR_INVALID_ARG;
-    if (flags & (KNNG_FLAG_REORDER | KNNG_FLAG_REORDER_B)) return KNNG_ERR_UNSUPPORTED;
+}  // extern "C"
+
+namespace {
+
+// One batched build over data sets of one row-width class (below).
+int build_batched_group(const knng_desc *descs, int count, int K, float rho, float delta, int max_iters,
+                        uint64_t seed, uint32_t flags, void *stream, knng_stats *stats) {
     int64_t ntot = 0;
     int dmax = 0;
     std::vector<long long> off(count + 1);
@@ -822,6 +825,76 @@ int knng_build_batched(const knng_desc *descs, int count, int K, float rho, floa
         if (r3) rc = r3;
     }
     knng_destroy(c);
+    return rc;
+}
+
+// Row-width classes of the batched build: a data set is padded to the
+// smallest class width >= d (at most 1.5x its row), so narrow data sets do
+// not pay for the widest one and take the join kernel that suits their width.
+int width_class(int d) {
+    if (d > (1 << 24)) return d;
+    int w = 32;
+    while (w < d) w = (w % 3 == 0) ? w / 3 * 4 : w / 2 * 3;  // 32, 48, 64, 96, 128, 192, 256, ...
+    return w;
+}
+
+void add_stats(knng_stats &a, const knng_stats &b) {
+    a.n += b.n;
+    a.d = std::max(a.d, b.d);
+    a.K = b.K;
+    a.s = b.s;
+    a.iterations = std::max(a.iterations, b.iterations);
+    a.dist_evals += b.dist_evals;
+    a.last_changes += b.last_changes;
+    a.inserts += b.inserts;
+    a.merges += b.merges;
+    a.gathered_rows += b.gathered_rows;
+    a.rev_overflow += b.rev_overflow;
+    a.set_overflow += b.set_overflow;
+    a.lock_timeouts += b.lock_timeouts;
+    a.kernel_launches += b.kernel_launches;
+    a.cand_ids += b.cand_ids;
+    a.proposals += b.proposals;
+    a.bucket_overflow += b.bucket_overflow;
+    a.join_launches += b.join_launches;
+    a.join_ms += b.join_ms;
+    a.join_ran += b.join_ran;
+    a.join_path = b.join_path;
+    a.join_ms_ran += b.join_ms_ran;
+    a.merge_ms_ran += b.merge_ms_ran;
+}
+
+}  // namespace
+
+extern "C" {
+
+int knng_build_batched(const knng_desc *descs, int count, int K, float rho, float delta, int max_iters,
+                       uint64_t seed, uint32_t flags, void *stream, knng_stats *stats) {
+    if (!descs || count < 1 || max_iters < 0 || max_iters > kMaxItersArg) return KNNG_ERR_INVALID_ARG;
+    if (flags & (KNNG_FLAG_REORDER | KNNG_FLAG_REORDER_B)) return KNNG_ERR_UNSUPPORTED;
+    for (int b = 0; b < count; ++b)
+        if (descs[b].d < 1) return KNNG_ERR_INVALID_ARG;
+    // one batched build per row-width class, widest last
+    std::vector<int> cls(count);
+    for (int b = 0; b < count; ++b) cls[b] = width_class(descs[b].d);
+    std::vector<int> widths(cls);
+    std::sort(widths.begin(), widths.end());
+    widths.erase(std::unique(widths.begin(), widths.end()), widths.end());
+    knng_stats total;
+    std::memset(&total, 0, sizeof(total));
+    int rc = KNNG_OK;
+    for (int w : widths) {
+        std::vector<knng_desc> g;
+        for (int b = 0; b < count; ++b)
+            if (cls[b] == w) g.push_back(descs[b]);
+        knng_stats gs;
+        const int r = build_batched_group(g.data(), (int)g.size(), K, rho, delta, max_iters, seed, flags, stream,
+                                          stats ? &gs : nullptr);
+        if (r < 0) return r;
+        if (r > 0) rc = r;
+        if (stats) add_stats(total, gs);
+    }
+    if (stats) *stats = total;
     return rc;
 }
 
