@@ -344,10 +344,14 @@ def test_uniform_n2k_recall_and_invariants():
     assert abs(rg - ro) <= 0.005
 
 
-def test_graph_capture_gives_the_same_graph():
-    x = workloads.gaussian_mixture(4000, 16, 12, seed=6)
-    a_i, a_d, sa = knng.knng_build(_cuda(x), 12, 0.5, 0.001, 10, seed=1)
-    b_i, b_d, sb = knng.knng_build(_cuda(x), 12, 0.5, 0.001, 10, seed=1, flags=knng.FLAG_GRAPH)
+@pytest.mark.parametrize("flags", [0, knng.FLAG_REORDER, knng.FLAG_BF16])
+def test_graph_capture_gives_the_same_graph(flags):
+    """The captured-graph loop and one-by-one launches build the same graph,
+    also with the relabelling and bf16 staging inside the captured loop."""
+    d = 72 if flags == knng.FLAG_BF16 else 16
+    x = workloads.gaussian_mixture(4000, d, 12, seed=6)
+    a_i, a_d, sa = knng.knng_build(_cuda(x), 12, 0.5, 0.001, 10, seed=1, flags=flags)
+    b_i, b_d, sb = knng.knng_build(_cuda(x), 12, 0.5, 0.001, 10, seed=1, flags=flags | knng.FLAG_GRAPH)
     assert (a_i.cpu().numpy() == b_i.cpu().numpy()).all() and (a_d.cpu().numpy() == b_d.cpu().numpy()).all()
     assert sa["iterations"] == sb["iterations"] and sa["dist_evals"] == sb["dist_evals"]
 
