@@ -207,7 +207,8 @@ def run_batched(args):
     all_sets = workloads.batched_data(cfg["count"], cfg["seed"])
     sets = all_sets[rank::ws]
     xs = [torch.from_numpy(x).to(device) for x in sets]
-    flags = (knng.FLAG_BF16 if args.bf16 else 0) | (knng.FLAG_GRAPH if args.graph else 0)
+    flags = (knng.FLAG_BF16 if args.bf16 else 0) | (knng.FLAG_GRAPH if args.graph else 0) | \
+        (knng.FLAG_AUTOTUNE if args.autotune else 0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     K, rho, delta, it = cfg["K"], cfg["rho"], cfg["delta"], cfg["max_iters"]
 
@@ -270,6 +271,7 @@ def run_batched(args):
         "config": {"workload": "batched_256", "datasets": len(all_sets),
                    "total_n": int(sum(len(x) for x in all_sets)), "K": K, "rho": rho, "delta": delta,
                    "max_iters": it, "bf16": bool(args.bf16), "graph": bool(args.graph),
+                   "autotune": bool(args.autotune),
                    "parallelism": f"datasets round-robin over {ws} rank(s)",
                    "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
         "e2e": {"value": round(ve, 6), "unit": "s", "h2d_bytes_per_step": int(sum(x.nbytes for x in sets)),
@@ -302,7 +304,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     flags = (knng.FLAG_REORDER if args.reorder else 0) | (knng.FLAG_BF16 if args.bf16 else 0) | \
-        (knng.FLAG_GRAPH if args.graph else 0)
+        (knng.FLAG_GRAPH if args.graph else 0) | (knng.FLAG_AUTOTUNE if args.autotune else 0)
     dp = (w.d + 3) // 4 * 4
     if args.bf16 and w.d >= 64:
         dp = (w.d + 63) // 64 * 64 // 2  # bf16 rows: half the bytes of float32
@@ -393,7 +395,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if args.bf16 else "f32", "data": "synthetic",
         "config": {"workload": wname, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
                    "max_iters": w.max_iters, "reorder": bool(args.reorder), "bf16": bool(args.bf16),
-                   "graph": bool(args.graph), "parallelism": f"replicas{ws}",
+                   "graph": bool(args.graph), "autotune": bool(args.autotune), "join_path": stats["join_path"],
+                   "parallelism": f"replicas{ws}",
                    "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
         "recall_at_k": round(rec, 5), "recall_rows": RECALL_ROWS,
         "iterations": stats["iterations"], "dist_evals": stats["dist_evals"],
@@ -471,6 +474,7 @@ def main():
     ap.add_argument("--reorder", action="store_true", help="Algorithm 1 relabelling after iteration 1")
     ap.add_argument("--bf16", action="store_true", help="bf16 tensor-core dots for d >= 64, float32 re-rank")
     ap.add_argument("--graph", action="store_true", help="launch the iteration loop as one captured CUDA graph")
+    ap.add_argument("--autotune", action="store_true", help="time the join kernels on the first build, keep the fastest")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["batched_256"],
                     help="another workload than the headline one (measurement table)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")

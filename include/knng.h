@@ -60,6 +60,9 @@ extern "C" {
 #define KNNG_FLAG_GRAPH 0x8u     /* knng_run: capture the iteration loop as one CUDA graph and launch it */
 #define KNNG_FLAG_BF16 0x10u     /* d >= 64: local-join dots in bf16 on the tensor cores (float32
                                     accumulate, |x|^2+|y|^2-2x.y); output re-ranked in float32 */
+#define KNNG_FLAG_AUTOTUNE 0x20u /* time every join kernel the geometry allows on the first iteration of the
+                                    first context with this geometry (d, K, precision) in the process, and
+                                    use the fastest from then on; that iteration synchronises */
 
 typedef struct knng_ctx knng_ctx;
 

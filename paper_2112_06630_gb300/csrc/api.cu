@@ -7,6 +7,8 @@
 #include <cstdlib>
 #include <algorithm>
 #include <cstring>
+#include <array>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -111,6 +113,7 @@ struct knng_ctx {
     int it_done = 0;    // absolute iterations done (selects the random streams)
     int li = 0;         // iterations launched by this context
     bool reordered = false;
+    bool tune_pending = false;  // KNNG_FLAG_AUTOTUNE: the first iteration times the join kernels
     long long launches = 0;
 
     unsigned char *arena = nullptr;
@@ -189,6 +192,13 @@ struct knng_ctx {
 
 namespace {
 
+// Join kernels chosen by the autotuner, per geometry (bf16, row width, K,
+// reverse capacity), for the life of the process.
+std::mutex g_tune_mu;
+std::map<std::array<int, 4>, int> g_tune_cache;
+
+std::array<int, 4> tune_key(const knng_ctx *c) { return {c->bf16 ? 1 : 0, c->bf16 ? c->dpb : c->dp, c->K, c->R}; }
+
 int ctx_alloc(knng_ctx *c) {
     const int64_t n = c->n;
     const bool reorder = (c->flags & KNNG_FLAG_REORDER) != 0;
@@ -215,7 +225,8 @@ int ctx_alloc(knng_ctx *c) {
     const size_t oE = take(sizeof(int));
     const size_t oXb = c->bf16 ? take(sizeof(uint16_t) * n * c->dpb) : 0;
     const size_t oXn = c->bf16 ? take(sizeof(float) * n) : 0;
-    const bool ring = c->join_path == kJoinRing;
+    const bool ring = c->join_path == kJoinRing ||
+                      (c->tune_pending && ring_join_fits(c->bf16, c->nv, c->dpb, c->K));
     const size_t oCs = ring ? take(sizeof(int) * (size_t)n * kSetMax) : 0;
     const size_t oCm = ring ? take(sizeof(int) * (size_t)n) : 0;
     cudaError_t e = lib_malloc((void **)&c->arena, off, c->stream);
@@ -328,6 +339,12 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
         else if (!std::strcmp(e, "ring")) force = kJoinRing;
     }
     c->join_path = choose_join_path(c->bf16, c->nv, c->dpb, K, force);
+    if ((flags & KNNG_FLAG_AUTOTUNE) && force < 0) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(tune_key(c));
+        if (it != g_tune_cache.end()) c->join_path = it->second;
+        else c->tune_pending = true;
+    }
     c->stream = (cudaStream_t)stream;
     c->thr = (double)delta * (double)n * (double)K;
     rc = ctx_alloc(c);
@@ -378,12 +395,77 @@ int enqueue_reorder(knng_ctx *c) {
 }
 
 // One iteration: count, sample, join (+ Algorithm 1 after the first one).
+// Time every join kernel the context can run on its current (first)
+// iteration, between the sampling and the real join.  Each trial's side
+// effects are undone: bucket cursors, chunk tables and pool cursor zeroed,
+// the lists (which a full bucket's locked insertion may touch), the global
+// counters and the iteration's counters restored.  Synchronises the stream.
+int autotune_join(knng_ctx *c, int li) {
+    std::vector<int> paths = {kJoinTile};
+    if (!c->bf16) paths.push_back(kJoinWarp);
+    if (ring_join_fits(c->bf16, c->nv, c->dpb, c->K) && c->cset) paths.push_back(kJoinRing);
+    const size_t kb = sizeof(uint64_t) * (size_t)c->n * c->K;
+    unsigned char *tmp = nullptr;
+    KNNG_TRY(lib_malloc((void **)&tmp, align256(kb) + sizeof(long long) * kStatCount, c->stream));
+    uint64_t *keys0 = (uint64_t *)tmp;
+    long long *stats0 = (long long *)(tmp + align256(kb));
+    KNNG_TRY(cudaMemcpyAsync(keys0, c->keys, kb, cudaMemcpyDeviceToDevice, c->stream));
+    KNNG_TRY(cudaMemcpyAsync(stats0, c->stats, sizeof(long long) * kStatCount, cudaMemcpyDeviceToDevice, c->stream));
+    std::vector<cudaEvent_t> ev(2 * paths.size());
+    for (auto &e : ev) KNNG_TRY(cudaEventCreate(&e));
+    int rc = KNNG_OK;
+    for (size_t i = 0; i < paths.size() && !rc; ++i) {
+        const int keep = c->join_path;
+        c->join_path = paths[i];
+        DevState st = c->dev(false);
+        c->join_path = keep;
+        cudaError_t e = cudaEventRecord(ev[2 * i], c->stream);
+        if (e == cudaSuccess) e = launch_join(st, li, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i + 1], c->stream);
+        c->launches += join_launches(paths[i]);
+        // undo the trial
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->pcursor, 0, sizeof(int) * (size_t)c->n, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c->pchunk, 0, sizeof(int) * ((size_t)c->n * kBucketChunks + 1), c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->keys, keys0, kb, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->stats, stats0, sizeof(long long) * kStatCount, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c->it_stats + (size_t)li * kItCount, 0, sizeof(long long) * kItCount, c->stream);
+        if (e != cudaSuccess) rc = cuda_code(e);
+    }
+    if (!rc) rc = cuda_code(cudaStreamSynchronize(c->stream));
+    int best = c->join_path;
+    float best_ms = 0.f;
+    for (size_t i = 0; i < paths.size() && !rc; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) != cudaSuccess) continue;
+        if (i == 0 || ms < best_ms) {
+            best = paths[i];
+            best_ms = ms;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    cudaFreeAsync(tmp, c->stream);
+    if (rc) return rc;
+    c->join_path = best;
+    c->tune_pending = false;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[tune_key(c)] = best;
+    return KNNG_OK;
+}
+
 int enqueue_iteration(knng_ctx *c, bool gate) {
     if (c->li >= kMaxLocalIters) return KNNG_ERR_STATE;
     const int li = c->li, it = c->it_done + 1;
     DevState st = c->dev(gate);
     KNNG_TRY(launch_count(st, li, c->stream));
     KNNG_TRY(launch_sample(st, li, it, c->seed, c->stream));
+    if (c->tune_pending) {
+        int rc = autotune_join(c, li);
+        if (rc) return rc;
+        st = c->dev(gate);
+    }
     const bool timing = (c->flags & KNNG_FLAG_TIMING) != 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     if (timing) {
@@ -507,6 +589,12 @@ int knng_iterate(knng_ctx *c, int64_t *changes_out) {
 
 int knng_run(knng_ctx *c, int max_iters) {
     if (!c || max_iters < 0 || max_iters > kMaxItersArg) return KNNG_ERR_INVALID_ARG;
+    if (c->tune_pending && max_iters > 0) {
+        // the tuning iteration synchronises: it runs before any capture
+        int rc = enqueue_iteration(c, true);
+        if (rc) return rc;
+        --max_iters;
+    }
     const bool graph = (c->flags & KNNG_FLAG_GRAPH) && max_iters > 0;
     if (!graph) {
         for (int t = 0; t < max_iters; ++t) {

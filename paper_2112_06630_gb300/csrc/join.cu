@@ -311,31 +311,73 @@ __device__ __forceinline__ int warp_sort_merge(uint64_t &Lk, uint64_t x, int K, 
     return __popc(__ballot_sync(kFull, valid && rank_c < K));
 }
 
+// bf16 mode: the two orientations of a pair may round to different keys, so
+// an id can come with several.  The list keeps, per id, the smallest key seen
+// (whatever the arrival order): of repeats in one batch only the smallest
+// stays, and a smaller key for a listed id replaces the listed entry.
+// Returns true when x is to be inserted as a new id; replacements are done
+// here (rare).
+__device__ __forceinline__ bool bf16_resolve_ids(uint64_t &Lk, uint64_t &x, int K, int &ins) {
+    const unsigned lane = lane_id();
+    const bool real = x != kKeyEmpty;
+    const uint32_t xi = key_id(x);
+    // repeats within the batch
+    const unsigned peers = __match_any_sync(kFull, real ? xi : 0xFFFFFFFFu);
+    if (__any_sync(kFull, real && __popc(peers) > 1)) {
+        bool keep = true;
+        for (int l = 0; l < 32; ++l) {
+            const uint64_t y = __shfl_sync(kFull, x, l);
+            if (real && y != kKeyEmpty && key_id(y) == xi && (y < x || (y == x && l < (int)lane))) keep = false;
+        }
+        if (!keep) x = kKeyEmpty;
+    }
+    // the id in the list
+    uint64_t listed_key = kKeyEmpty;
+    for (int k = 0; k < K; ++k) {
+        const uint64_t lk = __shfl_sync(kFull, Lk, k);
+        if (x != kKeyEmpty && key_id(lk) == xi) listed_key = lk;
+    }
+    // smaller keys of listed ids replace their entries, one at a time
+    unsigned rep = __ballot_sync(kFull, x != kKeyEmpty && listed_key != kKeyEmpty && x < listed_key);
+    for (; rep; rep &= rep - 1) {
+        const int l = __ffs(rep) - 1;
+        const uint64_t y = __shfl_sync(kFull, x, l);
+        const unsigned at = __ballot_sync(kFull, (int)lane < K && key_id(Lk) == key_id(y));
+        if (!at) continue;            // (cannot happen: ids in one batch are distinct)
+        const int p = __ffs(at) - 1;  // the listed entry: drop it, close the gap
+        const uint64_t below = __shfl_down_sync(kFull, Lk, 1);
+        if ((int)lane >= p && (int)lane < K) Lk = (int)lane == K - 1 ? kKeyEmpty : below;
+        ins += warp_insert(Lk, y, K);
+    }
+    return x != kKeyEmpty && listed_key == kKeyEmpty;
+}
+
 // One batch of up to 32 bucket keys (one per lane, kKeyEmpty = none) into
 // the list held one entry per lane.  Keys that cannot enter are dropped in
 // parallel: not before the worst, or already listed (a pair has one key, so
 // "listed" is "the same (dist, id) at its lower bound", a binary search over
-// the lanes; bf16 keys of a pair may differ from its float32 key in the list,
-// so there the id is looked up).  Returns the number of insertions.
+// the lanes; bf16 mode resolves ids as above).  Returns the number of
+// insertions.
 __device__ __forceinline__ int merge_batch(uint64_t &Lk, uint64_t x, int K, bool bf16, uint64_t *scratch) {
-    const uint64_t xo = key_order(x);
-    int lo = 0, hi = K - 1;
-#pragma unroll
-    for (int step = 0; step < 5; ++step) {
-        const int mid = (lo + hi) >> 1;
-        const uint64_t lm = __shfl_sync(kFull, Lk, mid);
-        if (lo < hi) {
-            if (key_order(lm) < xo) lo = mid + 1;
-            else hi = mid;
-        }
-    }
-    bool listed = key_order(__shfl_sync(kFull, Lk, lo)) == xo;
+    int ins = 0;
+    bool listed;
     if (bf16) {
-        const uint32_t xi = key_id(x);
-        for (int k = 0; k < K; ++k) listed |= key_id(__shfl_sync(kFull, Lk, k)) == xi;
+        listed = !bf16_resolve_ids(Lk, x, K, ins);
+    } else {
+        const uint64_t xo = key_order(x);
+        int lo = 0, hi = K - 1;
+#pragma unroll
+        for (int step = 0; step < 5; ++step) {
+            const int mid = (lo + hi) >> 1;
+            const uint64_t lm = __shfl_sync(kFull, Lk, mid);
+            if (lo < hi) {
+                if (key_order(lm) < xo) lo = mid + 1;
+                else hi = mid;
+            }
+        }
+        listed = key_order(__shfl_sync(kFull, Lk, lo)) == xo;
     }
     unsigned cand = __ballot_sync(kFull, x < __shfl_sync(kFull, Lk, K - 1) && !listed);
-    int ins = 0;
     if (__popc(cand) >= kSortMergeMin) {
         ins += warp_sort_merge(Lk, ((cand >> lane_id()) & 1u) ? x : kKeyEmpty, K, scratch);
     } else {

@@ -300,7 +300,13 @@ __global__ void __launch_bounds__(kTileThreads) tile_join_kernel(DevState st, in
                         }
                         drop = key_order(Lt[lo]) == xo;
                     } else if (!drop) {
-                        for (int k = 0; k < K && !drop; ++k) drop = key_id(Lt[k]) == q;
+                        // bf16: a listed id is kept only with its smaller key
+                        // (the merge keeps each id's smallest key)
+                        for (int k = 0; k < K; ++k)
+                            if (key_id(Lt[k]) == q) {
+                                drop = key_order(Lt[k]) <= key_order(x);
+                                break;
+                            }
                     }
                     if (drop) mt &= ~(1ull << j);
                 }

@@ -419,3 +419,40 @@ def test_batched_equals_single_builds_float_data():
     for x, (bi, bd) in zip(sets, outs):
         si, sd, _ = knng.knng_build(_cuda(x), 16, 0.5, 0.001, 15, seed=9)
         assert (bi == si.cpu().numpy()).all() and (bd == sd.cpu().numpy()).all()
+
+
+# -------------------------------------------------------------- autotuner ----
+
+def test_autotuned_builds_equal_default_builds():
+    """KNNG_FLAG_AUTOTUNE times every eligible join kernel on the first
+    iteration, undoes each trial and keeps the fastest: the graph is the same
+    bit for bit (every kernel computes the same pairs and keys), and the
+    second build of the geometry reuses the choice."""
+    x = workloads.gaussian_mixture(5000, 48, 15, seed=9)
+    ref_i, ref_d, _ = knng.knng_build(_cuda(x), 16, 0.5, 0.001, 8, seed=4)
+    a_i, a_d, sa = knng.knng_build(_cuda(x), 16, 0.5, 0.001, 8, seed=4, flags=knng.FLAG_AUTOTUNE)
+    b_i, b_d, sb = knng.knng_build(_cuda(x), 16, 0.5, 0.001, 8, seed=4, flags=knng.FLAG_AUTOTUNE)
+    assert torch.equal(a_i, ref_i) and torch.equal(a_d, ref_d)
+    assert torch.equal(b_i, ref_i) and torch.equal(b_d, ref_d)
+    assert sa["join_path"] in (0, 1, 2) and sb["join_path"] == sa["join_path"]
+    # the tuning build ran three trial joins on top of the real ones
+    assert sa["kernel_launches"] > sb["kernel_launches"]
+
+
+def test_autotuned_bf16_and_batched_match_the_oracle():
+    x = _int_data(900, 96, 4, seed=96)
+    ids0, new0 = workloads.random_graph(900, 16, seed=97, p_new=0.6)
+    with knng.Context(_cuda(x), 16, rho=0.5, seed=5, graph=(ids0, new0), iter=0,
+                      flags=knng.FLAG_BF16 | knng.FLAG_AUTOTUNE) as c:
+        c.iterate()
+        gi, gd, gf = c.state()
+    st = oracle.State(x, 16, 0.5, seed=5)
+    st.init_graph(ids0, new0, 0)
+    st.iterate()
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    sets = [_int_data(n, d, 4, seed=n) for n, d in [(700, 20), (1500, 40), (900, 100)]]
+    outs, _ = knng.knng_build_batched([_cuda(s) for s in sets], 10, 0.5, 0.001, 6, seed=2, flags=knng.FLAG_AUTOTUNE)
+    for s, (bi, bd) in zip(sets, outs):
+        oi, od, _ = oracle.build_knng(s, 10, 0.5, 0.001, 6, seed=2)
+        assert (bi.cpu().numpy() == oi).all()
