@@ -321,9 +321,11 @@ __device__ __forceinline__ bool bf16_resolve_ids(uint64_t &Lk, uint64_t &x, int 
     const unsigned lane = lane_id();
     const bool real = x != kKeyEmpty;
     const uint32_t xi = key_id(x);
-    // repeats within the batch
+    // repeats within the batch with different keys (equal keys are one key:
+    // the insertions skip a listed id, the sort-merge drops equal neighbours)
     const unsigned peers = __match_any_sync(kFull, real ? xi : 0xFFFFFFFFu);
-    if (__any_sync(kFull, real && __popc(peers) > 1)) {
+    const unsigned same = __match_any_sync(kFull, (unsigned long long)x);
+    if (__any_sync(kFull, real && peers != same)) {
         bool keep = true;
         for (int l = 0; l < 32; ++l) {
             const uint64_t y = __shfl_sync(kFull, x, l);
