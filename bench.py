@@ -286,6 +286,55 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def run_sweep(args):
+    """Dimension sweep (the paper's d = 8 ... 3144 in steps of 64 at n =
+    16,384 on the Single Gaussian set, covariance 2 I; K = 20, rho = 0.5,
+    delta = 0.001, at most 15 iterations), float32 and bf16, then the two
+    roofline placements at n = 131,072, d in {8, 256}.  One JSON line per
+    run: build time, local-join time per launch, distance evaluations per
+    second, the paper's flop rate (evals * (3d - 1) / s) and the join's
+    achieved bytes per second."""
+    import torch
+
+    import paper_2112_06630_gb300 as knng
+
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    K, rho, delta, it = 20, 0.5, 0.001, 15
+    runs = [(16384, d) for d in range(8, 3145, 64)] + [(131072, 8), (131072, 256)]
+    for n, d in runs:
+        x = torch.from_numpy(workloads.single_gaussian(n, d, seed=d, var=2.0)).to(device)
+        for bf16 in (False, True):
+            if bf16 and d < 64:
+                continue
+            flags = knng.FLAG_BF16 if bf16 else 0
+            for _ in range(2):
+                knng.knng_build(x, K, rho, delta, it, seed=0, flags=flags)
+            ts = []
+            for _ in range(3):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                s0 = torch.cuda.Event(enable_timing=True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                s0.record()
+                _, _, st = knng.knng_build(x, K, rho, delta, it, seed=0, flags=flags)
+                e0.record()
+                torch.cuda.synchronize()
+                ts.append(s0.elapsed_time(e0) / 1e3)
+            _, _, tst = knng.knng_build(x, K, rho, delta, it, seed=0, flags=flags | knng.FLAG_TIMING)
+            t = sum(ts) / len(ts)
+            ran = max(1, tst["join_ran"])
+            dp = (d + 63) // 64 * 32 if bf16 and d >= 64 else (d + 3) // 4 * 4
+            jt = tst["join_ms_ran"] / 1e3 / ran
+            print(json.dumps({"sweep": "dimension", "n": n, "d": d, "bf16": bf16, "build_s": round(t, 6),
+                              "iterations": st["iterations"], "join_path": st["join_path"],
+                              "join_ms_per_launch": round(jt * 1e3, 4),
+                              "dist_evals_per_s": round(st["dist_evals"] / t, 1),
+                              "paper_flops_per_s": round(st["dist_evals"] * (3 * d - 1) / t, 1),
+                              "join_gb_per_s": round(join_bytes(tst, dp) / ran / jt / 1e9, 1)}), flush=True)
+
+
 def run_gpu(args):
     import torch
 
@@ -478,6 +527,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["batched_256"],
                     help="another workload than the headline one (measurement table)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
+    ap.add_argument("--sweep-d", action="store_true", help="dimension sweep at n=16,384 (one JSON line per run)")
     ap.add_argument("--n", type=int, default=None, help="override the workload's point count (profiling)")
     ap.add_argument("--rho", type=float, default=None, help="override the sample rate (recall sweeps)")
     ap.add_argument("--delta", type=float, default=None, help="override the termination threshold")
@@ -486,7 +536,9 @@ def main():
     if args.warmup < 3 and args.impl == "gb300":
         print("note: at least 3 warm-up steps are required; using 3", file=sys.stderr)
         args.warmup = 3
-    if args.impl == "reference":
+    if args.sweep_d:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched_256":
         if any(v is not None for v in (args.n, args.rho, args.delta, args.max_iters)):

@@ -78,3 +78,22 @@ def test_batched_workload_slice_equals_single_builds():
     for x, (bi, bd) in zip(xs, outs):
         si, sd, _ = knng.knng_build(x, cfg["K"], cfg["rho"], cfg["delta"], cfg["max_iters"], seed=0)
         assert torch.equal(bi, si) and torch.equal(bd, sd)
+
+
+def test_audio_like_n54k_d192_full_size_plain_and_relabelled():
+    """Audio-shaped 54,387 x 192 (K=20, rho=0.5): plain and Algorithm-1
+    relabelled builds both meet the invariants and the same recall level
+    (the relabelling changes the visiting order of the nodes, not the
+    method's graph quality)."""
+    w, x = workloads.make("audio_like_n54k_d192")
+    xd = torch.from_numpy(x).cuda()
+    rows = np.random.default_rng(3).choice(w.n, 1000, replace=False)
+    bi, _ = knng.knng_bruteforce(xd, w.K, rows=torch.from_numpy(rows).cuda())
+    bi = bi.cpu().numpy()
+    rec = {}
+    for flags in (0, knng.FLAG_REORDER):
+        gi, gd, st = knng.knng_build(xd, w.K, w.rho, w.delta, w.max_iters, seed=0, flags=flags)
+        gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+        assert metrics.check_graph(x, gi, gd, rows=rows) == []
+        rec[flags] = metrics.recall(x, gi, bi, rows)
+    assert rec[0] >= 0.97 and abs(rec[0] - rec[knng.FLAG_REORDER]) <= 0.01, rec

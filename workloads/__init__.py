@@ -22,7 +22,7 @@ import numpy as np
 
 __all__ = [
     "Workload", "WORKLOADS", "uniform", "gaussian_mixture", "single_gaussian",
-    "mnist_like", "batched_specs", "random_graph", "make",
+    "mnist_like", "audio_like", "batched_specs", "random_graph", "make",
 ]
 
 
@@ -106,6 +106,41 @@ def mnist_like(n: int = 70_000, d: int = 784, seed: int = 0, prototypes: int = 1
     return x
 
 
+def audio_like(n: int = 54_387, d: int = 192, seed: int = 0, sentences: int = 500, latent: int = 12,
+               corr: float = 0.9, noise: float = 0.1, return_labels: bool = False):
+    """Audio-shaped stand-in (the Audio set: 54,387 frames of 192 features
+    from spoken English sentences; not available): frames of `sentences`
+    utterances of random lengths, each utterance a smooth trajectory in a
+    `latent`-dimensional space (AR(1) with coefficient `corr`, unit
+    stationary variance) mapped to d features by one fixed random linear map
+    (N(0, 1/latent) entries), plus a per-utterance offset (N(0, 0.5^2)) and
+    per-feature noise N(0, noise^2).  Consecutive frames are close, as
+    spectral frames of speech are; float32."""
+    g = _rng(seed)
+    A = g.standard_normal((d, latent)) / math.sqrt(latent)
+    cuts = np.sort(g.choice(np.arange(1, n), sentences - 1, replace=False))
+    lengths = np.diff(np.concatenate([[0], cuts, [n]]))
+    x = np.empty((n, d), dtype=np.float64)
+    labels = np.empty(n, dtype=np.int32)
+    pos = 0
+    innov = math.sqrt(1.0 - corr * corr)
+    for s_, L in enumerate(lengths):
+        z = np.empty((L, latent))
+        z[0] = g.standard_normal(latent)
+        eps = g.standard_normal((L, latent)) * innov
+        for t in range(1, L):
+            z[t] = corr * z[t - 1] + eps[t]
+        off = g.standard_normal(d) * 0.5
+        x[pos:pos + L] = z @ A.T + off
+        labels[pos:pos + L] = s_
+        pos += L
+    x += g.standard_normal((n, d)) * noise
+    x = x.astype(np.float32)
+    if return_labels:
+        return x, labels
+    return x
+
+
 def batched_specs(count: int = 256, seed: int = 0):
     """Sizes for the batched workload: n ~ U{500..50000}, d ~ {32, 96, 128},
     clusters ~ U{5..50}; dataset i is drawn with generator seed 1000 + i."""
@@ -162,6 +197,8 @@ class Workload:
             return mnist_like(self.n, self.d, seed=self.seed, **p)
         if self.kind == "single_gaussian":
             return single_gaussian(self.n, self.d, seed=self.seed, **p)
+        if self.kind == "audio_like":
+            return audio_like(self.n, self.d, seed=self.seed, **p)
         raise ValueError(self.kind)
 
 
@@ -174,6 +211,8 @@ WORKLOADS = {
     # MNIST-shaped integer data
     "mnist_like_n70k_d784": Workload("mnist_like_n70k_d784", 70_000, 784, 20, 0.5, 0.001, 15,
                                      "mnist_like"),
+    # Audio-shaped: 54,387 x 192 frames of 500 smooth utterances
+    "audio_like_n54k_d192": Workload("audio_like_n54k_d192", 54_387, 192, 20, 0.5, 0.001, 15, "audio_like"),
     # large dense, 1000 clusters, centres N(0, 4I), sigma 0.5
     "mixture_n1m_d128": Workload("mixture_n1m_d128", 1_000_000, 128, 32, 0.3, 0.001, 12,
                                  "mixture", (("clusters", 1000), ("centre_std", 2.0),
