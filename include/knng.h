@@ -225,6 +225,17 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
                     int64_t nq, int32_t *ids, float *dists, void *stream);
 
 /*
+ * Diagnostic of the calling thread's last knng_bruteforce: for rows of at most
+ * 128 floats (and n >= 4096) the distance block runs on the tensor cores as a
+ * bf16 split Gram prefilter whose kept candidates are re-ranked with exact
+ * float32 distances; a query whose result the error bound cannot certify is
+ * recomputed by the exact kernel.  Returns how many queries were recomputed,
+ * or -1 when the last call did not take the tensor-core path.  The results
+ * are the same either way.
+ */
+int knng_bruteforce_last_fallbacks(void);
+
+/*
  * Brute-force K-NNG that allocates nothing, for callers that cannot allocate
  * device memory: code that runs while a stream is being captured into a CUDA
  * graph in global capture mode (where cudaMalloc is refused), programs whose

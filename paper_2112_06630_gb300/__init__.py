@@ -18,6 +18,7 @@ from . import build as _build
 
 __all__ = [
     "KnngError", "Stats", "Context", "knng_build", "knng_build_batched", "knng_bruteforce", "lib_path", "Desc",
+    "bruteforce_last_fallbacks",
     "FLAG_REORDER", "FLAG_REORDER_B", "FLAG_TIMING", "FLAG_GRAPH", "FLAG_BF16", "FLAG_AUTOTUNE", "version", "strerror", "load",
 ]
 
@@ -87,6 +88,7 @@ def _load():
         "knng_get_stats": (i32, [P, P]),
         "knng_destroy": (i32, [P]),
         "knng_bruteforce": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
+        "knng_bruteforce_last_fallbacks": (i32, []),
         "knng_build_batched": (i32, [P, i32, i32, f32, f32, i32, u64, u32, P, P]),
         "knng_strerror": (ctypes.c_char_p, [i32]),
         "knng_version": (ctypes.c_char_p, []),
@@ -240,6 +242,12 @@ def knng_bruteforce(data, K: int, rows=None, stream=None):
     ids, dists, ip, dp = _outputs(nq, K, dev, keep if dev else None)
     _check(_lib.knng_bruteforce(ptr, n, d, K, rp, nq, ip, dp, _stream_ptr(stream, dev)), "knng_bruteforce")
     return ids, dists
+
+
+def bruteforce_last_fallbacks() -> int:
+    """Queries of this thread's last knng_bruteforce that the tensor-core
+    prefilter could not certify (recomputed exactly); -1 if it did not run."""
+    return int(_lib.knng_bruteforce_last_fallbacks())
 
 
 class Context:

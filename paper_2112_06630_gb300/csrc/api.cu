@@ -192,6 +192,9 @@ struct knng_ctx {
 
 namespace {
 
+// knng_bruteforce_last_fallbacks: this thread's last tensor-core brute force
+thread_local int g_bf_fallbacks = -1;
+
 // Join kernels chosen by the autotuner, per geometry (bf16, row width, K,
 // reverse capacity), for the life of the process.
 std::mutex g_tune_mu;
@@ -986,6 +989,8 @@ int knng_build_batched(const knng_desc *descs, int count, int K, float rho, floa
     return rc;
 }
 
+int knng_bruteforce_last_fallbacks(void) { return g_bf_fallbacks; }
+
 int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *rows, int64_t nq, int32_t *ids,
                     float *dists, void *stream) {
     if (!data || !ids || !dists || n < 2 || d < 1 || K < 1 || K > n - 1) return KNNG_ERR_INVALID_ARG;
@@ -1028,7 +1033,31 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
         oi = (int32_t *)(tmp + xb + rb);
         od = (float *)(tmp + xb + rb + ib);
     }
-    if (e == cudaSuccess) e = launch_bruteforce(X, n, dp, K, rows_d, nq, oi, od, s, part, S);
+    // tensor-core prefilter with exact re-rank where the rows allow it
+    // (KNNG_TEST_BF_PATH=cuda|tensor forces a path in tests)
+    const char *force = std::getenv("KNNG_TEST_BF_PATH");
+    bool tc = bruteforce_tc_supported(dp) && n >= 4096;
+    if (force && !std::strcmp(force, "cuda")) tc = false;
+    if (force && !std::strcmp(force, "tensor")) tc = bruteforce_tc_supported(dp);
+    g_bf_fallbacks = -1;
+    if (e == cudaSuccess && tc) {
+        int TS = 1, nredo = 0;
+        unsigned char *tcs = nullptr;
+        const size_t tb = bruteforce_tc_scratch(n, nq, dp, K, &TS);
+        e = lib_malloc((void **)&tcs, tb, s);
+        if (e == cudaSuccess) {
+            e = launch_bruteforce_tc(X, n, dp, d, K, rows_d, nq, oi, od, s, tcs, TS, &nredo);
+            cudaFreeAsync(tcs, s);
+        }
+        if (e == cudaErrorNotSupported) {  // no tensor map encoder: the exact kernel
+            cudaGetLastError();
+            e = cudaSuccess;
+            tc = false;
+        } else if (e == cudaSuccess) {
+            g_bf_fallbacks = nredo;
+        }
+    }
+    if (e == cudaSuccess && !tc) e = launch_bruteforce(X, n, dp, K, rows_d, nq, oi, od, s, part, S);
     if (e == cudaSuccess && !dev_out) {
         e = cudaMemcpyAsync(ids, oi, sizeof(int32_t) * nq * K, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dists, od, sizeof(float) * nq * K, cudaMemcpyDeviceToHost, s);

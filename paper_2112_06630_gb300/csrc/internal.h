@@ -50,5 +50,13 @@ cudaError_t launch_bruteforce(const float *X, int64_t n, int dp, int K, const in
                               int32_t *ids, float *dists, cudaStream_t s, uint64_t *part, int S);
 // slices that give every SM work for nq queries over n points
 int bruteforce_slices(int64_t n, int64_t nq);
+// tensor-core brute force (bf16 split Gram prefilter, exact re-rank, exact
+// fallback per uncertified query): rows of at most 128 floats, and a driver
+// that encodes tensor maps
+bool bruteforce_tc_supported(int dp);
+size_t bruteforce_tc_scratch(int64_t n, int64_t nq, int dp, int K, int *slices_out);
+cudaError_t launch_bruteforce_tc(const float *X, int64_t n, int dp, int d, int K, const int64_t *rows, int64_t nq,
+                                 int32_t *ids, float *dists, cudaStream_t s, unsigned char *scratch, int S,
+                                 int *nredo_host);
 
 }  // namespace knng

@@ -63,6 +63,61 @@ def test_bruteforce_integer_data_bit_exact_with_ties():
     assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
 
 
+TC_CASES = [
+    # n, d, K, rows (None = all), data kind
+    (6000, 16, 20, None, "mix"),
+    (20000, 128, 32, 700, "mix"),
+    (9000, 8, 10, None, "int"),      # many equal distances: ties by id
+    (50000, 64, 16, 500, "mix"),
+    (8191, 100, 32, 333, "int"),     # ragged last tile and slice, padded rows
+]
+
+
+@pytest.mark.parametrize("n,d,K,nrows,kind", TC_CASES)
+def test_tensor_core_bruteforce_equals_exact_kernel(n, d, K, nrows, kind, monkeypatch):
+    """The tcgen05 split-bf16 prefilter with exact re-rank (and exact
+    recomputation of uncertified queries) returns the same ids and distances,
+    bit for bit, as the CUDA-core kernel that evaluates every pair."""
+    x = _int_data(n, d, 5, seed=n) if kind == "int" else workloads.gaussian_mixture(n, d, 30, seed=n)
+    rows = None if nrows is None else torch.from_numpy(np.random.default_rng(1).choice(n, nrows, replace=False)).cuda()
+    monkeypatch.setenv("KNNG_TEST_BF_PATH", "tensor")
+    ti, td = knng.knng_bruteforce(_cuda(x), K, rows=rows)
+    fallbacks = knng.bruteforce_last_fallbacks()
+    monkeypatch.setenv("KNNG_TEST_BF_PATH", "cuda")
+    ci, cd = knng.knng_bruteforce(_cuda(x), K, rows=rows)
+    assert knng.bruteforce_last_fallbacks() == -1
+    assert fallbacks >= 0
+    assert torch.equal(ti, ci) and torch.equal(td, cd)
+    if kind == "mix":  # real-valued data: the bound certifies nearly every query
+        assert fallbacks <= 0.05 * ti.shape[0], fallbacks
+
+
+def test_tensor_core_bruteforce_offset_data_and_fallbacks(monkeypatch):
+    """Data far from the origin (non-negative features plus an offset): the
+    prefilter centres the points, so the error bound stays small and almost
+    every query is certified.  Integer data with many equal distances sends
+    queries to the exact kernel (sliced over the points); both give the exact
+    kernel's answer bit for bit."""
+    g = np.random.default_rng(7)
+    x = (g.random((30000, 64), dtype=np.float32) + 50.0).astype(np.float32)
+    monkeypatch.setenv("KNNG_TEST_BF_PATH", "tensor")
+    ti, td = knng.knng_bruteforce(_cuda(x), 20)
+    fb = knng.bruteforce_last_fallbacks()
+    monkeypatch.setenv("KNNG_TEST_BF_PATH", "cuda")
+    ci, cd = knng.knng_bruteforce(_cuda(x), 20)
+    assert torch.equal(ti, ci) and torch.equal(td, cd)
+    assert 0 <= fb <= 0.05 * x.shape[0], fb
+    xi = _int_data(40000, 8, 4, seed=3)
+    rows = torch.arange(0, 40000, 37, device="cuda")
+    monkeypatch.setenv("KNNG_TEST_BF_PATH", "tensor")
+    ti, td = knng.knng_bruteforce(_cuda(xi), 16, rows=rows)
+    fb = knng.bruteforce_last_fallbacks()
+    monkeypatch.setenv("KNNG_TEST_BF_PATH", "cuda")
+    ci, cd = knng.knng_bruteforce(_cuda(xi), 16, rows=rows)
+    assert fb > 0
+    assert torch.equal(ti, ci) and torch.equal(td, cd)
+
+
 def test_bruteforce_query_rows_and_host_pointers():
     x = workloads.gaussian_mixture(5000, 16, 20, seed=3)
     rows = np.array([0, 4999, 17, 2500, 1234], np.int64)
