@@ -335,6 +335,105 @@ def run_sweep(args):
                               "join_gb_per_s": round(join_bytes(tst, dp) / ran / jt / 1e9, 1)}), flush=True)
 
 
+def run_bruteforce(args):
+    """Exact K-NNG by brute force (Section 2 definition; the ground truth) on
+    the workload's points: all rows, or --rows R sampled query rows.  One JSON
+    line: seconds per call with device-resident input, the end-to-end call
+    from pinned host memory, the pair rate, the roofline of the tensor-core
+    prefilter (its bf16 MMA work: three products of 2 * dpb flops for each
+    padded query-point pair, against the measured cuBLAS bf16 peak) and the
+    oracle on a bounded sample of queries."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2112_06630_gb300 as knng
+
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    w, x, wname = _workload(args)
+    n, d, K = x.shape[0], x.shape[1], w.K
+    nq = n if not args.rows else min(args.rows, n)
+    rows_h = None if nq == n else np.sort(np.random.default_rng(0).choice(n, nq, replace=False)).astype(np.int64)
+    xd = torch.from_numpy(x).to(device)
+    rows_d = None if rows_h is None else torch.from_numpy(rows_h).to(device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    for _ in range(args.warmup):
+        knng.knng_bruteforce(xd, K, rows=rows_d)
+    torch.cuda.synchronize()
+    ts, pf, fb = [], [], []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            s0 = torch.cuda.Event(enable_timing=True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            s0.record()
+            knng.knng_bruteforce(xd, K, rows=rows_d)
+            e0.record()
+            torch.cuda.synchronize()
+            ts.append(s0.elapsed_time(e0) / 1e3)
+            pf.append(knng.bruteforce_last_prefilter_ms())
+            fb.append(knng.bruteforce_last_fallbacks())
+    step_s = sum(ts) / len(ts)
+    # end to end: pinned host input and query ids, host outputs
+    xh = torch.from_numpy(x).pin_memory()
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        knng.knng_bruteforce(xh, K, rows=rows_h)
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e[args.warmup:]) / args.steps
+    tensor = pf[0] >= 0
+    roof = None
+    if tensor:
+        peaks = _peaks()
+        peak = peaks["bf16_tflops"] if peaks else 1900.0
+        dpb = ((d + 3) // 4 * 4 + 15) // 16 * 16
+        pad = lambda v: (v + 127) // 128 * 128
+        flops = 3.0 * 2.0 * dpb * pad(nq) * pad(n)
+        pms = sum(pf) / len(pf) / 1e3
+        ach = flops / pms / 1e12
+        roof = {"kernel": "bf_tc_kernel", "bound": "tensor", "achieved": round(ach, 1), "peak": peak,
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": "measured bf16 burst" if peaks else "fallback",
+                "flops_per_launch": flops, "launch_ms": round(pms * 1e3, 4),
+                "share_of_call": round(pms / step_s, 3)}
+    cpu = None
+    if not args.no_cpu:
+        # the oracle on a bounded sample of queries, scaled to the whole call
+        g = np.random.default_rng(1)
+        sample, spent, t0 = 0, 0.0, time.perf_counter()
+        while spent < 10.0 and sample < nq:
+            q = int(g.integers(0, n)) if rows_h is None else int(rows_h[g.integers(0, nq)])
+            oracle.bruteforce(x, K, rows=np.array([q], dtype=np.int64))
+            sample += 1
+            spent = time.perf_counter() - t0
+        cpu = {"value": round(spent / sample * nq, 3), "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"{sample} query rows against all {n} points, scaled to {nq} queries"}
+    launches = (7 + (3 if max(fb) > 0 else 0)) if tensor else 3
+    line = {
+        "metric": "exact K-NNG rows by brute force, s per call", "value": round(step_s, 6), "unit": "s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 prefilter + f32" if tensor else "f32", "data": "synthetic",
+        "config": {"workload": wname, "n": n, "d": d, "K": K, "queries": nq,
+                   "path": "tensor cores" if tensor else "CUDA cores",
+                   "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
+        "pairs_per_s": round(nq * (n - 1) / step_s, 1),
+        "uncertified_queries": fb[-1],
+        "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": int(x.nbytes) + (0 if rows_h is None
+                else int(rows_h.nbytes)), "d2h_bytes_per_step": int(nq * K * 8)},
+        "gpu_launches": launches * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args):
     import torch
 
@@ -528,6 +627,8 @@ def main():
                     help="another workload than the headline one (measurement table)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
     ap.add_argument("--sweep-d", action="store_true", help="dimension sweep at n=16,384 (one JSON line per run)")
+    ap.add_argument("--bruteforce", action="store_true", help="time the exact brute-force K-NNG on the workload")
+    ap.add_argument("--rows", type=int, default=0, help="brute force: sampled query rows (0 = every row)")
     ap.add_argument("--n", type=int, default=None, help="override the workload's point count (profiling)")
     ap.add_argument("--rho", type=float, default=None, help="override the sample rate (recall sweeps)")
     ap.add_argument("--delta", type=float, default=None, help="override the termination threshold")
@@ -538,6 +639,8 @@ def main():
         args.warmup = 3
     if args.sweep_d:
         run_sweep(args)
+    elif args.bruteforce and args.impl == "gb300":
+        run_bruteforce(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched_256":

@@ -219,7 +219,10 @@ int knng_build_batched(const knng_desc *descs, int count, int K, float rho, floa
  * Exact K-NNG by brute force (Section 2: every distance, the K smallest per
  * point by (dist, id), float32 difference-form distances).  rows (host or
  * device int64, may be NULL = all n rows) selects nq query points; outputs
- * are nq x K.  Ground truth for recall.
+ * are nq x K.  Ground truth for recall.  For rows of at most 128 floats and
+ * n >= 4096 the call waits for the stream before it returns (it reads how many
+ * queries the exact kernel must redo; see knng_bruteforce_last_fallbacks);
+ * otherwise it only enqueues work when ids and dists are device pointers.
  */
 int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *rows,
                     int64_t nq, int32_t *ids, float *dists, void *stream);
@@ -234,6 +237,14 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
  * are the same either way.
  */
 int knng_bruteforce_last_fallbacks(void);
+
+/*
+ * Diagnostic of the calling thread's last knng_bruteforce: the CUDA-event
+ * time in milliseconds of its tensor-core prefilter kernel (the dense part of
+ * the call; split, re-rank and exact recomputation excluded), or -1 when the
+ * last call did not take the tensor-core path.
+ */
+float knng_bruteforce_last_prefilter_ms(void);
 
 /*
  * Brute-force K-NNG that allocates nothing, for callers that cannot allocate

@@ -18,7 +18,7 @@ from . import build as _build
 
 __all__ = [
     "KnngError", "Stats", "Context", "knng_build", "knng_build_batched", "knng_bruteforce", "lib_path", "Desc",
-    "bruteforce_last_fallbacks",
+    "bruteforce_last_fallbacks", "bruteforce_last_prefilter_ms",
     "FLAG_REORDER", "FLAG_REORDER_B", "FLAG_TIMING", "FLAG_GRAPH", "FLAG_BF16", "FLAG_AUTOTUNE", "version", "strerror", "load",
 ]
 
@@ -89,6 +89,7 @@ def _load():
         "knng_destroy": (i32, [P]),
         "knng_bruteforce": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
         "knng_bruteforce_last_fallbacks": (i32, []),
+        "knng_bruteforce_last_prefilter_ms": (f32, []),
         "knng_build_batched": (i32, [P, i32, i32, f32, f32, i32, u64, u32, P, P]),
         "knng_strerror": (ctypes.c_char_p, [i32]),
         "knng_version": (ctypes.c_char_p, []),
@@ -248,6 +249,12 @@ def bruteforce_last_fallbacks() -> int:
     """Queries of this thread's last knng_bruteforce that the tensor-core
     prefilter could not certify (recomputed exactly); -1 if it did not run."""
     return int(_lib.knng_bruteforce_last_fallbacks())
+
+
+def bruteforce_last_prefilter_ms() -> float:
+    """CUDA-event time of this thread's last tensor-core prefilter kernel in
+    milliseconds; -1 if the last knng_bruteforce did not take that path."""
+    return float(_lib.knng_bruteforce_last_prefilter_ms())
 
 
 class Context:

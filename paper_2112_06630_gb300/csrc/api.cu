@@ -194,6 +194,7 @@ namespace {
 
 // knng_bruteforce_last_fallbacks: this thread's last tensor-core brute force
 thread_local int g_bf_fallbacks = -1;
+thread_local float g_bf_prefilter_ms = -1.f;
 
 // Join kernels chosen by the autotuner, per geometry (bf16, row width, K,
 // reverse capacity), for the life of the process.
@@ -991,6 +992,8 @@ int knng_build_batched(const knng_desc *descs, int count, int K, float rho, floa
 
 int knng_bruteforce_last_fallbacks(void) { return g_bf_fallbacks; }
 
+float knng_bruteforce_last_prefilter_ms(void) { return g_bf_prefilter_ms; }
+
 int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *rows, int64_t nq, int32_t *ids,
                     float *dists, void *stream) {
     if (!data || !ids || !dists || n < 2 || d < 1 || K < 1 || K > n - 1) return KNNG_ERR_INVALID_ARG;
@@ -1040,13 +1043,15 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
     if (force && !std::strcmp(force, "cuda")) tc = false;
     if (force && !std::strcmp(force, "tensor")) tc = bruteforce_tc_supported(dp);
     g_bf_fallbacks = -1;
+    g_bf_prefilter_ms = -1.f;
     if (e == cudaSuccess && tc) {
         int TS = 1, nredo = 0;
+        float pf_ms = -1.f;
         unsigned char *tcs = nullptr;
         const size_t tb = bruteforce_tc_scratch(n, nq, dp, K, &TS);
         e = lib_malloc((void **)&tcs, tb, s);
         if (e == cudaSuccess) {
-            e = launch_bruteforce_tc(X, n, dp, d, K, rows_d, nq, oi, od, s, tcs, TS, &nredo);
+            e = launch_bruteforce_tc(X, n, dp, d, K, rows_d, nq, oi, od, s, tcs, TS, &nredo, &pf_ms);
             cudaFreeAsync(tcs, s);
         }
         if (e == cudaErrorNotSupported) {  // no tensor map encoder: the exact kernel
@@ -1055,6 +1060,7 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
             tc = false;
         } else if (e == cudaSuccess) {
             g_bf_fallbacks = nredo;
+            g_bf_prefilter_ms = pf_ms;
         }
     }
     if (e == cudaSuccess && !tc) e = launch_bruteforce(X, n, dp, K, rows_d, nq, oi, od, s, part, S);

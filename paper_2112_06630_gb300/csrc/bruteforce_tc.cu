@@ -114,6 +114,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
           "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(addr));
 }
+// three-input minimum (sm_100 and later)
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 struct TcShared {
@@ -296,7 +302,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         uint64_t L[32];
 #pragma unroll
         for (int k = 0; k < 32; ++k) L[k] = kKeyEmpty;
-        uint32_t thr = 0xFFFFFFFFu;  // distance bits of L[31]: every candidate passes until the list is full
+        float thr = INFINITY;  // distance of L[31]: every candidate passes until the list is full
         bool ok = true;
         // the 64 columns' squared norms, one per lane and half, loaded a tile ahead
         auto norms = [&](int64_t t, float &xa, float &xb) {
@@ -323,28 +329,42 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int64_t c0 = t * kTcRows + h * 64;
             const float xa = na, xb = nb;
             norms(t + 1, na, nb);
-            // existing columns other than the query itself
-            const int64_t nval = n - c0;
-            uint64_t valid = nval >= 64 ? ~0ull : (nval <= 0 ? 0ull : (1ull << nval) - 1);
-            if (self >= c0 && self < c0 + 64) valid &= ~(1ull << (self - c0));
-            // pass 1 (straight-line): D' for all 64 columns and the mask of those
-            // not above the current 32nd; the list update below is one copy of
-            // the insertion network, entered rarely once the list is full
-            uint32_t m0 = 0, m1 = 0;
+            // pass 1 (straight-line): the unclamped D' of all 64 columns and
+            // their minimum.  Rounding is monotone and thr >= 0, so some
+            // column has max(0, D') <= thr exactly when the minimum does; only
+            // then is the tile scanned again column by column, with one copy
+            // of the insertion network
+            float lo = INFINITY;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float dd = fmaxf(0.f, qnorm + __shfl_sync(kFull, xa, j) - 2.f * __uint_as_float(v0[j]));
-                v0[j] = __float_as_uint(dd);
-                m0 |= (v0[j] <= thr ? 1u : 0u) << j;
+            for (int j = 0; j < 32; j += 2) {
+                const float e0 = qnorm + __shfl_sync(kFull, xa, j) - 2.f * __uint_as_float(v0[j]);
+                const float e1 = qnorm + __shfl_sync(kFull, xa, j + 1) - 2.f * __uint_as_float(v0[j + 1]);
+                v0[j] = __float_as_uint(e0);
+                v0[j + 1] = __float_as_uint(e1);
+                lo = fmin3(lo, e0, e1);
             }
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float dd = fmaxf(0.f, qnorm + __shfl_sync(kFull, xb, j) - 2.f * __uint_as_float(v1[j]));
-                v1[j] = __float_as_uint(dd);
-                m1 |= (v1[j] <= thr ? 1u : 0u) << j;
+            for (int j = 0; j < 32; j += 2) {
+                const float e0 = qnorm + __shfl_sync(kFull, xb, j) - 2.f * __uint_as_float(v1[j]);
+                const float e1 = qnorm + __shfl_sync(kFull, xb, j + 1) - 2.f * __uint_as_float(v1[j + 1]);
+                v1[j] = __float_as_uint(e0);
+                v1[j + 1] = __float_as_uint(e1);
+                lo = fmin3(lo, e0, e1);
             }
-            uint64_t m = ((uint64_t)m1 << 32 | m0) & valid;
-            if (m) {
+            if (lo <= thr) {
+                // existing columns other than the query itself
+                const int64_t nval = n - c0;
+                uint64_t m = nval >= 64 ? ~0ull : (nval <= 0 ? 0ull : (1ull << nval) - 1);
+                if (self >= c0 && self < c0 + 64) m &= ~(1ull << (self - c0));
+                uint32_t m0 = 0, m1 = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    v0[j] = __float_as_uint(fmaxf(0.f, __uint_as_float(v0[j])));
+                    v1[j] = __float_as_uint(fmaxf(0.f, __uint_as_float(v1[j])));
+                    m0 |= (__uint_as_float(v0[j]) <= thr ? 1u : 0u) << j;
+                    m1 |= (__uint_as_float(v1[j]) <= thr ? 1u : 0u) << j;
+                }
+                m &= (uint64_t)m1 << 32 | m0;
                 uint32_t buf[64];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
@@ -363,7 +383,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         L[0] = L[0] < x ? L[0] : x;
                     }
                 }
-                thr = (uint32_t)(L[31] >> 32);
+                if (L[31] != kKeyEmpty) thr = key_dist(L[31]);
             }
         }
         if (!ok) sh.abort_flag = 1;
@@ -422,6 +442,8 @@ __global__ void __launch_bounds__(256) bf_rerank_kernel(const float4 *__restrict
                                                         int64_t *__restrict__ redo, int *__restrict__ nredo) {
     const unsigned lane = lane_id();
     const float xmax = sqrtf(__uint_as_float(*nmax));
+    // squared norms this large could overflow D' to +inf: nothing is certified
+    const bool huge = __uint_as_float(*nmax) >= 1.2676506e30f;  // 2^100
     for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq;
          q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int64_t self = qrow ? qrow[q] : q;
@@ -456,7 +478,7 @@ __global__ void __launch_bounds__(256) bf_rerank_kernel(const float4 *__restrict
         const float dot_rel = 3.1f * 1.52587890625e-5f + 3.0f * (float)d * 5.9604645e-8f;
         const float E = 2.f * (2.f * dot_rel * qa * xmax + 4.768371582e-7f * (qa + xmax) * (qa + xmax));
         const float dk = key_dist(__shfl_sync(kFull, ea, K - 1));
-        const bool ok = (T - E) * (1.f - 4.f * (float)d * 5.9604645e-8f) > dk;
+        const bool ok = !huge && (T - E) * (1.f - 4.f * (float)d * 5.9604645e-8f) > dk;
         if ((int)lane < K) {
             ids[(size_t)q * K + lane] = (int32_t)key_id(ea);
             dists[(size_t)q * K + lane] = key_dist(ea);
@@ -545,10 +567,21 @@ size_t bruteforce_tc_scratch(int64_t n, int64_t nq, int dp, int K, int *slices_o
 
 bool bruteforce_tc_supported(int dp) { return ((dp + 15) & ~15) <= 128 && encode_fn() != nullptr; }
 
-// nredo_host: the number of queries the exact kernel redid (statistics)
+namespace {
+// CUDA events around the prefilter launch, per thread, made on first use on
+// each device (the call waits for its stream anyway, so reading them is free)
+struct PrefilterEvents {
+    int dev = -1;
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+thread_local PrefilterEvents g_pf_events;
+}  // namespace
+
+// nredo_host: the number of queries the exact kernel redid; prefilter_ms:
+// the prefilter kernel's CUDA-event time (statistics)
 cudaError_t launch_bruteforce_tc(const float *X, int64_t n, int dp, int d, int K, const int64_t *rows, int64_t nq,
                                  int32_t *ids, float *dists, cudaStream_t s, unsigned char *scratch, int S,
-                                 int *nredo_host) {
+                                 int *nredo_host, float *prefilter_ms) {
     const int dpb = (dp + 15) & ~15;
     const int64_t npad = (n + kTcRows - 1) / kTcRows * kTcRows, qpad = (nq + kTcRows - 1) / kTcRows * kTcRows;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -596,9 +629,18 @@ cudaError_t launch_bruteforce_tc(const float *X, int64_t n, int dp, int d, int K
         opted = true;
     }
     const int64_t ntiles = npad / kTcRows, per = (ntiles + S - 1) / S;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    PrefilterEvents &ev = g_pf_events;
+    if (ev.dev != dev) {
+        if ((e = cudaEventCreate(&ev.a)) != cudaSuccess || (e = cudaEventCreate(&ev.b)) != cudaSuccess) return e;
+        ev.dev = dev;
+    }
+    if ((e = cudaEventRecord(ev.a, s)) != cudaSuccess) return e;
     bf_tc_kernel<<<dim3((unsigned)(qpad / kTcRows), (unsigned)S), kTcThreads, dyn, s>>>(
         mqh, mql, mxh, mxl, qn, xn, rows, nq, n, dpb, per, part, counters + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev.b, s)) != cudaSuccess) return e;
     const int gr = grid_for((const void *)bf_rerank_kernel, 256, 0);
     bf_rerank_kernel<<<gr, 256, 0, s>>>(reinterpret_cast<const float4 *>(X), dp / 4, d, rows, nq, K, 2 * S, part, qn,
                                        (const unsigned *)(counters + 2), ids, dists, redo, counters);
@@ -606,6 +648,7 @@ cudaError_t launch_bruteforce_tc(const float *X, int64_t n, int dp, int d, int K
     int hc[2] = {0, 0};
     if ((e = cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (prefilter_ms && cudaEventElapsedTime(prefilter_ms, ev.a, ev.b) != cudaSuccess) *prefilter_ms = -1.f;
     if (hc[1]) return cudaErrorLaunchTimeout;  // a bounded wait gave up
     if (nredo_host) *nredo_host = hc[0];
     if (hc[0] == 0) return cudaSuccess;

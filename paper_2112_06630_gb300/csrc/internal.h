@@ -57,6 +57,6 @@ bool bruteforce_tc_supported(int dp);
 size_t bruteforce_tc_scratch(int64_t n, int64_t nq, int dp, int K, int *slices_out);
 cudaError_t launch_bruteforce_tc(const float *X, int64_t n, int dp, int d, int K, const int64_t *rows, int64_t nq,
                                  int32_t *ids, float *dists, cudaStream_t s, unsigned char *scratch, int S,
-                                 int *nredo_host);
+                                 int *nredo_host, float *prefilter_ms);
 
 }  // namespace knng
