@@ -52,6 +52,8 @@ def _load():
             "orc_init_random": (i32, [P]),
             "orc_init_graph": (i32, [P, P, P, i32]),
             "orc_sample": (i32, [P, i32, P]),
+            "orc_sample_heap": (i32, [P, i32, P]),
+            "orc_set_sampler": (i32, [P, i32]),
             "orc_join": (i32, [P, P]),
             "orc_iterate": (i32, [P, P]),
             "orc_reorder": (i32, [P, i32]),
@@ -62,7 +64,7 @@ def _load():
             "orc_get_sigma": (i32, [P, P]),
             "orc_free": (None, [P]),
             "orc_greedy_reorder": (i32, [P, i64, i32, i32, P, P]),
-            "orc_build": (i32, [P, i64, i32, i32, f32, f32, i32, u64, i32, i32, P, P, P]),
+            "orc_build": (i32, [P, i64, i32, i32, f32, f32, i32, u64, i32, i32, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -80,7 +82,8 @@ def _f32(data) -> np.ndarray:
     return np.ascontiguousarray(data, dtype=np.float32)
 
 
-STREAM_INIT, STREAM_FWD, STREAM_REV = 1, 2, 3
+STREAM_INIT, STREAM_FWD, STREAM_REV, STREAM_HEAP = 1, 2, 3, 4
+SAMPLERS = {"turbo": 0, "heap": 1}
 
 
 def hash64(seed: int, stream: int, it: int, u: int, j: int) -> int:
@@ -93,9 +96,10 @@ def dist64(x, y) -> float:
 
 
 def sample_size(rho: float, K: int) -> int:
-    """s = ceil(rho * K), clamped to [1, K] (same rule as the C code)."""
+    """s = ceil(rho * K), clamped to [1, K] (same rule as the C code: rho as
+    float32, with a tolerance that absorbs its rounding)."""
     import math
-    return max(1, min(K, int(math.ceil(rho * K - 1e-9))))
+    return max(1, min(K, int(math.ceil(float(np.float32(rho)) * K - 1e-5))))
 
 
 def bruteforce(data, K: int, rows=None):
@@ -128,15 +132,17 @@ def greedy_reorder(lists, reading_b: bool = False):
 
 
 def build_knng(data, K: int, rho: float, delta: float, max_iters: int, seed: int = 0,
-               count_mode: str = "batched", reorder: int = 0):
-    """Whole NN-Descent.  Returns (ids, dists, stats dict)."""
+               count_mode: str = "batched", reorder: int = 0, sampler: str = "turbo"):
+    """Whole NN-Descent.  sampler: "turbo" (Section 3.1's one-pass
+    probability sampling) or "heap" (priority heaps).  Returns (ids, dists,
+    stats dict)."""
     data = _f32(data)
     n, d = data.shape
     ids = np.empty((n, K), np.int32)
     dists = np.empty((n, K), np.float32)
     st = np.zeros(4, np.int64)
     rc = _load().orc_build(_p(data), n, d, K, rho, delta, max_iters, seed,
-                           1 if count_mode == "inplace" else 0, int(reorder),
+                           1 if count_mode == "inplace" else 0, int(reorder), SAMPLERS[sampler],
                            _p(ids), _p(dists), _p(st))
     if rc:
         raise ValueError(f"orc_build failed ({rc})")
@@ -147,15 +153,17 @@ def build_knng(data, K: int, rho: float, delta: float, max_iters: int, seed: int
 class State:
     """Step-by-step NN-Descent state (for step-level parity tests)."""
 
-    def __init__(self, data, K: int, rho: float, seed: int = 0):
+    def __init__(self, data, K: int, rho: float, seed: int = 0, sampler: str = "turbo"):
         self._data = _f32(data)
         self.n, self.d = self._data.shape
         self.K = K
         self.s = sample_size(rho, K)
+        self.sampler = sampler
         self._lib = _load()
         self._h = self._lib.orc_create(_p(self._data), self.n, self.d, K, rho, seed)
         if not self._h:
             raise ValueError("orc_create: invalid arguments")
+        self._lib.orc_set_sampler(self._h, SAMPLERS[sampler])
 
     def close(self):
         if self._h:
@@ -176,7 +184,8 @@ class State:
 
     def sample(self, it: int):
         st = np.zeros(3, np.int64)
-        if self._lib.orc_sample(self._h, it, _p(st)):
+        fn = self._lib.orc_sample_heap if self.sampler == "heap" else self._lib.orc_sample
+        if fn(self._h, it, _p(st)):
             raise MemoryError
         return dict(max_rev_new=int(st[0]), max_rev_old=int(st[1]), max_cands=int(st[2]))
 

@@ -46,7 +46,7 @@
 #define ORC_NEW 1u   /* entry not yet sampled as a "new" forward candidate */
 #define ORC_INS 2u   /* entry inserted during the current iteration        */
 
-enum { ORC_STREAM_INIT = 1, ORC_STREAM_FWD = 2, ORC_STREAM_REV = 3 };
+enum { ORC_STREAM_INIT = 1, ORC_STREAM_FWD = 2, ORC_STREAM_REV = 3, ORC_STREAM_HEAP = 4 };
 
 /* ---------------------------------------------------------------- RNG ---- */
 
@@ -186,16 +186,19 @@ typedef struct {
     orc_entry *lists;       /* n x K, ascending (dist, id) */
     int32_t *sigma;         /* new position of original node u; identity until reordered */
     int reordered;
+    int sampler;            /* 0: turbosampling (Section 3.1), 1: priority heaps */
     /* per-iteration scratch */
     int32_t **new_c, **old_c;
     int32_t *new_n, *old_n;
     int32_t *cap_new, *cap_old;
 } orc_state;
 
+/* s = ceil(rho K); the tolerance absorbs the float32 rounding of rho (0.3f x
+ * 10 = 3.0000001 must give 3). */
 static int orc_ceil_rho_k(float rho, int K)
 {
     double v = (double)rho * (double)K;
-    int s = (int)ceil(v - 1e-9);
+    int s = (int)ceil(v - 1e-5);
     if (s < 1) s = 1;
     if (s > K) s = K;
     return s;
@@ -414,6 +417,136 @@ out:
  * q enters p's list iff (dist, q) orders before the worst entry and q is not
  * already listed; the worst entry leaves.  Returns 1 on insertion.
  */
+/*
+ * Selection step, priority-heap variant: the candidate construction of
+ * PyNNDescent, which Section 3.1 sets turbosampling against.  Edge e = (u, j)
+ * with v = lists[u][j] and flag f draws one priority p_e = hi32(h(seed, HEAP,
+ * iter, u, j)) and offers v to u's candidates of kind f and u to v's
+ * candidates of kind f, both with priority p_e.  For each node x and kind f
+ * the offers are reduced to one per id (its smallest priority) and the s
+ * smallest by (priority, id) are kept: a uniform sample of s distinct
+ * candidates without replacement.  A forward "new" entry of x loses its flag
+ * when its id is kept among x's new candidates.  new[x] = the kept new ids,
+ * old[x] = the kept old ids not in new[x], both ascending by (priority, id).
+ *
+ * stats: [0] max reverse-new offers, [1] max reverse-old offers, [2] max |new|+|old|.
+ */
+typedef struct {
+    uint32_t p;
+    int32_t id;
+} orc_offer;
+
+static int orc_cmp_offer_id(const void *pa, const void *pb)
+{
+    const orc_offer *a = (const orc_offer *)pa, *b = (const orc_offer *)pb;
+    if (a->id != b->id) return a->id < b->id ? -1 : 1;
+    if (a->p != b->p) return a->p < b->p ? -1 : 1;
+    return 0;
+}
+
+static int orc_cmp_offer_p(const void *pa, const void *pb)
+{
+    const orc_offer *a = (const orc_offer *)pa, *b = (const orc_offer *)pb;
+    if (a->p != b->p) return a->p < b->p ? -1 : 1;
+    if (a->id != b->id) return a->id < b->id ? -1 : 1;
+    return 0;
+}
+
+int orc_sample_heap(orc_state *st, int iter, int64_t *stats)
+{
+    int64_t n = st->n;
+    int K = st->K, s = st->s;
+    int64_t *start = (int64_t *)calloc((size_t)(2 * n + 1), sizeof(int64_t));
+    int64_t *fill = (int64_t *)calloc((size_t)(2 * n), sizeof(int64_t));
+    orc_offer *rev = (orc_offer *)malloc(sizeof(orc_offer) * (size_t)(n * K + 1));
+    uint8_t *clear = (uint8_t *)calloc((size_t)n * (size_t)K, 1);
+    int rc = 0;
+    if (!start || !fill || !rev || !clear) {
+        rc = -2;
+        goto out;
+    }
+    /* reverse offers of node v and kind f (0 new, 1 old) at rev[start[2v+f] ..) */
+    for (int64_t u = 0; u < n; ++u)
+        for (int k = 0; k < K; ++k) {
+            const orc_entry *e = st->lists + u * K + k;
+            start[2 * (int64_t)e->id + ((e->flags & ORC_NEW) ? 0 : 1) + 1]++;
+        }
+    for (int64_t i = 0; i < 2 * n; ++i) start[i + 1] += start[i];
+    for (int64_t u = 0; u < n; ++u)
+        for (int k = 0; k < K; ++k) {
+            const orc_entry *e = st->lists + u * K + k;
+            int64_t slot = 2 * (int64_t)e->id + ((e->flags & ORC_NEW) ? 0 : 1);
+            orc_offer *o = rev + start[slot] + fill[slot]++;
+            o->p = (uint32_t)(orc_hash(st->seed, ORC_STREAM_HEAP, (uint32_t)iter, (uint64_t)u, (uint64_t)k) >> 32);
+            o->id = (int32_t)u;
+        }
+    int64_t mx_rn = 0, mx_ro = 0, mx_s = 0;
+    for (int64_t x = 0; x < n; ++x) {
+        int32_t kept[2][64];
+        int nkept[2] = {0, 0};
+        for (int f = 0; f < 2; ++f) {
+            int64_t nrev = start[2 * x + f + 1] - start[2 * x + f];
+            if (f == 0 && nrev > mx_rn) mx_rn = nrev;
+            if (f == 1 && nrev > mx_ro) mx_ro = nrev;
+            orc_offer *buf = (orc_offer *)malloc(sizeof(orc_offer) * (size_t)(K + nrev + 1));
+            if (!buf) { rc = -2; goto out; }
+            int64_t m = 0;
+            for (int k = 0; k < K; ++k) {
+                const orc_entry *e = st->lists + x * K + k;
+                if (((e->flags & ORC_NEW) ? 0 : 1) != f) continue;
+                buf[m].p = (uint32_t)(orc_hash(st->seed, ORC_STREAM_HEAP, (uint32_t)iter, (uint64_t)x, (uint64_t)k) >> 32);
+                buf[m].id = e->id;
+                ++m;
+            }
+            for (int64_t i = 0; i < nrev; ++i) buf[m++] = rev[start[2 * x + f] + i];
+            /* one offer per id: its smallest priority */
+            qsort(buf, (size_t)m, sizeof(orc_offer), orc_cmp_offer_id);
+            int64_t w = 0;
+            for (int64_t i = 0; i < m; ++i)
+                if (w == 0 || buf[w - 1].id != buf[i].id) buf[w++] = buf[i];
+            qsort(buf, (size_t)w, sizeof(orc_offer), orc_cmp_offer_p);
+            for (int64_t i = 0; i < w && i < s; ++i) kept[f][nkept[f]++] = buf[i].id;
+            free(buf);
+        }
+        st->new_n[x] = 0;
+        st->old_n[x] = 0;
+        for (int i = 0; i < nkept[0]; ++i)
+            if (orc_push(&st->new_c[x], &st->new_n[x], &st->cap_new[x], kept[0][i])) { rc = -2; goto out; }
+        for (int i = 0; i < nkept[1]; ++i) {
+            int dup = 0;
+            for (int t = 0; t < nkept[0]; ++t)
+                if (kept[0][t] == kept[1][i]) dup = 1;
+            if (!dup && orc_push(&st->old_c[x], &st->old_n[x], &st->cap_old[x], kept[1][i])) { rc = -2; goto out; }
+        }
+        for (int k = 0; k < K; ++k) {
+            const orc_entry *e = st->lists + x * K + k;
+            if (!(e->flags & ORC_NEW)) continue;
+            for (int t = 0; t < nkept[0]; ++t)
+                if (kept[0][t] == e->id) clear[x * K + k] = 1;
+        }
+        if (st->new_n[x] + st->old_n[x] > mx_s) mx_s = st->new_n[x] + st->old_n[x];
+    }
+    for (int64_t u = 0; u < n; ++u)
+        for (int k = 0; k < K; ++k)
+            if (clear[u * K + k]) st->lists[u * K + k].flags &= ~ORC_NEW;
+    if (stats) {
+        stats[0] = mx_rn;
+        stats[1] = mx_ro;
+        stats[2] = mx_s;
+    }
+out:
+    free(start); free(fill); free(rev); free(clear);
+    return rc;
+}
+
+/* Which selection step orc_iterate runs: 0 turbosampling, 1 priority heaps. */
+int orc_set_sampler(orc_state *st, int sampler)
+{
+    if (sampler != 0 && sampler != 1) return -1;
+    st->sampler = sampler;
+    return 0;
+}
+
 static int orc_update(orc_state *st, int32_t p, int32_t q, float dist)
 {
     int K = st->K;
@@ -598,7 +731,7 @@ int orc_reorder(orc_state *st, int reading_b)
 int orc_iterate(orc_state *st, int64_t *out)
 {
     int it = st->iter + 1;
-    int rc = orc_sample(st, it, out + 3);
+    int rc = st->sampler ? orc_sample_heap(st, it, out + 3) : orc_sample(st, it, out + 3);
     if (rc) return rc;
     rc = orc_join(st, out);
     if (rc) return rc;
@@ -666,16 +799,21 @@ void orc_free(orc_state *st)
  * delta * n * K or max_iters iterations have run.  count_mode 0 = batched
  * count (entries new to a list after the iteration), 1 = in-place count
  * (successful sequential insertions).  reorder: 0 none, 1 Algorithm 1 reading
- * A after the first iteration, 2 reading B.  stats (may be NULL), int64 x 4:
- * iterations run, total distance evaluations, last change count, reordered.
+ * A after the first iteration, 2 reading B.  sampler: 0 turbosampling, 1
+ * priority heaps.  stats (may be NULL), int64 x 4: iterations run, total
+ * distance evaluations, last change count, reordered.
  */
 int orc_build(const float *data, int64_t n, int d, int K, float rho, float delta,
-              int max_iters, uint64_t seed, int count_mode, int reorder,
+              int max_iters, uint64_t seed, int count_mode, int reorder, int sampler,
               int32_t *ids, float *dists, int64_t *stats)
 {
     if (delta < 0.0f || max_iters < 0) return -1;
     orc_state *st = orc_create(data, n, d, K, rho, seed);
     if (!st) return -1;
+    if (orc_set_sampler(st, sampler)) {
+        orc_free(st);
+        return -1;
+    }
     int rc = orc_init_random(st);
     int64_t evals = 0, last = 0;
     double thr = (double)delta * (double)n * (double)K;

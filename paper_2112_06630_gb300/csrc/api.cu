@@ -25,8 +25,10 @@ constexpr int kMaxItersArg = 1000;
 
 int rev_capacity(int s) { return 2 * s + 8; }
 
+// s = ceil(rho K); the tolerance absorbs the float32 rounding of rho (0.3f x
+// 10 = 3.0000001 must give 3), far below any fractional part of rho K
 int sample_size(float rho, int K) {
-    int s = (int)std::ceil((double)rho * (double)K - 1e-9);
+    int s = (int)std::ceil((double)rho * (double)K - 1e-5);
     if (s < 1) s = 1;
     if (s > K) s = K;
     return s;

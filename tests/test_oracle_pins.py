@@ -213,6 +213,131 @@ def test_sampling_reverse_mean_is_min_s_indegree():
     assert abs(got.sum() - np.minimum(s, indeg).sum()) < 5 * math.sqrt(var) + 1
 
 
+# ------------------------------------------------- priority-heap sampling ----
+
+def _bipartite(na, nb, K, seed):
+    """Sources 0..na-1 point at K sinks each with new edges; sinks point at K
+    sources each with old edges."""
+    g = np.random.default_rng(seed)
+    n = na + nb
+    ids = np.empty((n, K), np.int32)
+    is_new = np.zeros((n, K), np.uint8)
+    for u in range(na):
+        ids[u] = na + g.choice(nb, K, replace=False)
+        is_new[u] = 1
+    for b in range(na, n):
+        ids[b] = g.choice(na, K, replace=False)
+    return ids, is_new
+
+
+def test_heap_sampling_sizes_are_exact():
+    """The heap keeps the s smallest-priority distinct offers: a sink's new
+    candidates are exactly min(s, in-degree) of its in-neighbours, and a
+    source keeps exactly s of its K new forward entries (and clears exactly
+    those flags) -- where turbosampling only matches these in expectation."""
+    na, nb, K, rho = 1500, 150, 10, 0.5
+    s = oracle.sample_size(rho, K)
+    ids, is_new = _bipartite(na, nb, K, seed=4)
+    n = na + nb
+    st = oracle.State(workloads.uniform(n, 2, 1), K, rho, seed=7, sampler="heap")
+    st.init_graph(ids, is_new)
+    st.sample(1)
+    new, old = st.samples()
+    sid, _, flags = st.state()  # lists in their (dist, id) order
+    indeg = np.bincount(ids[:na].ravel(), minlength=n)
+    for b in range(na, n):
+        src = set(np.nonzero((ids[:na] == b).any(1))[0].tolist())
+        assert len(new[b]) == min(s, indeg[b]) and set(new[b].tolist()) <= src
+        assert len(set(new[b].tolist())) == len(new[b])
+    for a in range(na):
+        assert len(new[a]) == s and set(new[a].tolist()) <= set(ids[a].tolist())
+        cleared = set(sid[a][flags[a] == 0].tolist())
+        assert cleared == set(new[a].tolist())
+        assert len(old[a]) <= s
+    assert (flags[na:] == 0).all()  # sinks' entries were old already
+
+
+def test_heap_sampling_is_uniform_without_replacement():
+    """Each of a sink's m in-neighbours is kept with probability s / m over
+    fresh iterations (priorities redrawn per iteration): a chi-square test
+    over every (sink, in-neighbour) pair."""
+    na, nb, K, rho, T = 600, 60, 10, 0.3, 400
+    s = oracle.sample_size(rho, K)
+    ids, is_new = _bipartite(na, nb, K, seed=6)
+    n = na + nb
+    st = oracle.State(workloads.uniform(n, 2, 2), K, rho, seed=3, sampler="heap")
+    hits = np.zeros((n, n), np.int64)
+    for it in range(1, T + 1):
+        st.init_graph(ids, is_new, 0)
+        st.sample(it)
+        new, _ = st.samples()
+        for b in range(na, n):
+            hits[b, new[b]] += 1
+    chi, dof = 0.0, 0
+    for b in range(na, n):
+        src = np.nonzero((ids[:na] == b).any(1))[0]
+        m = len(src)
+        p = min(1.0, s / m)
+        if p >= 1.0:
+            assert (hits[b, src] == T).all()
+            continue
+        e = T * p
+        chi += (((hits[b, src] - e) ** 2) / (e * (1 - p))).sum()
+        dof += m
+    # chi-square with dof degrees of freedom: mean dof, sd sqrt(2 dof)
+    assert abs(chi - dof) < 5 * math.sqrt(2 * dof)
+
+
+def test_heap_sampling_one_offer_per_id():
+    """A symmetric ring (u lists its K nearest ring neighbours, all new) offers
+    every neighbour twice, forward and reverse: the kept sets hold distinct
+    ids, exactly s of them, each neighbour with frequency s / K."""
+    n, K, rho, T = 400, 8, 0.5, 300
+    s = oracle.sample_size(rho, K)
+    off = np.array([o for o in range(1, K // 2 + 1)] + [-o for o in range(1, K // 2 + 1)])
+    ids = ((np.arange(n)[:, None] + off[None, :]) % n).astype(np.int32)
+    is_new = np.ones((n, K), np.uint8)
+    st = oracle.State(workloads.uniform(n, 2, 3), K, rho, seed=5, sampler="heap")
+    freq = np.zeros((n, K), np.int64)
+    for it in range(1, T + 1):
+        st.init_graph(ids, is_new, 0)
+        st.sample(it)
+        new, old = st.samples()
+        for u in range(n):
+            assert len(new[u]) == s and len(set(new[u].tolist())) == s
+            assert set(new[u].tolist()) <= set(ids[u].tolist()) and len(old[u]) == 0
+            freq[u] += np.isin(ids[u], new[u])
+    p = s / K
+    mean = freq.mean() / T
+    assert abs(mean - p) < 5 * math.sqrt(p * (1 - p) / (T * n * K))
+
+
+def test_heap_sampling_takes_everything_at_rho_one():
+    """rho = 1 on the ring: s = K >= the K distinct offers, so every list
+    entry is kept as a new candidate and every flag is cleared."""
+    n, K = 300, 6
+    off = np.array([1, 2, 3, -1, -2, -3])
+    ids = ((np.arange(n)[:, None] + off[None, :]) % n).astype(np.int32)
+    st = oracle.State(workloads.uniform(n, 2, 4), K, 1.0, seed=1, sampler="heap")
+    st.init_graph(ids, np.ones((n, K), np.uint8))
+    st.sample(1)
+    new, old = st.samples()
+    _, _, flags = st.state()
+    assert (flags == 0).all()
+    for u in range(n):
+        assert set(new[u].tolist()) == set(ids[u].tolist()) and len(old[u]) == 0
+
+
+def test_heap_sampling_build_recall():
+    """Whole NN-Descent with the heap sampler on 2,000 uniform points in
+    [0,1)^8 (K=10, rho=1) reaches recall 0.99 like turbosampling."""
+    w, x = workloads.make("uniform_n2k_d8")
+    ei, _ = oracle.bruteforce(x, w.K)
+    oi, od, st = oracle.build_knng(x, w.K, w.rho, w.delta, w.max_iters, seed=0, sampler="heap")
+    assert metrics.check_graph(x, oi, od) == []
+    assert metrics.recall(x, oi, ei) >= 0.99
+
+
 # ---------------------------------------------------------------- join ----
 
 def test_join_all_pairs_reduces_to_topk():
