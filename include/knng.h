@@ -63,6 +63,12 @@ extern "C" {
 #define KNNG_FLAG_AUTOTUNE 0x20u /* time every join kernel the geometry allows on the first iteration of the
                                     first context with this geometry (d, K, precision) in the process, and
                                     use the fastest from then on; that iteration synchronises */
+#define KNNG_FLAG_HEAP_SAMPLING 0x40u /* candidate selection by priority heaps (PyNNDescent's construction)
+                                        instead of Section 3.1's turbosampling: edge (u, j) draws one
+                                        priority hi32(h(seed, 4, it, u, j)) for both of its offers (v to
+                                        u, u to v, of the edge's new/old kind); each node keeps per kind
+                                        the s smallest (priority, id) offers, one per id; forward new
+                                        entries kept as new candidates lose their flag */
 
 typedef struct knng_ctx knng_ctx;
 

@@ -122,6 +122,9 @@ struct knng_ctx {
     float *X = nullptr, *X2 = nullptr;
     uint64_t *keys = nullptr, *keys2 = nullptr;
     int *locks = nullptr, *ibuf = nullptr, *cand = nullptr, *err = nullptr, *pcursor = nullptr;
+    bool heap = false;  // KNNG_FLAG_HEAP_SAMPLING
+    int *hoff = nullptr, *hcursor = nullptr;
+    uint64_t *hcsr = nullptr;
     int *pchunk = nullptr, *pool_next = nullptr;
     uint16_t *Xb = nullptr, *Xb2 = nullptr;
     float *xnorm = nullptr, *xnorm2 = nullptr;
@@ -167,6 +170,9 @@ struct knng_ctx {
         st.fwd_old = ibuf + 5 * n;
         st.cand_new = cand;
         st.cand_old = cand + (size_t)n * cap;
+        st.hoff = hoff;
+        st.hcsr = hcsr;
+        st.hcursor = hcursor;
         st.stats = stats;
         st.it_stats = it_stats;
         st.n = n;
@@ -235,6 +241,8 @@ int ctx_alloc(knng_ctx *c) {
                       (c->tune_pending && ring_join_fits(c->bf16, c->nv, c->dpb, c->K));
     const size_t oCs = ring ? take(sizeof(int) * (size_t)n * kSetMax) : 0;
     const size_t oCm = ring ? take(sizeof(int) * (size_t)n) : 0;
+    const size_t oHo = c->heap ? take(sizeof(int) * (2 * (size_t)n + 1)) : 0;
+    const size_t oHc = c->heap ? take(sizeof(uint64_t) * (size_t)n * c->K) : 0;
     cudaError_t e = lib_malloc((void **)&c->arena, off, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -270,6 +278,11 @@ int ctx_alloc(knng_ctx *c) {
     if (ring) {
         c->cset = (int *)(a + oCs);
         c->cmeta = (int *)(a + oCm);
+    }
+    if (c->heap) {
+        c->hoff = (int *)(a + oHo);
+        c->hcursor = c->hoff + 2 * n;
+        c->hcsr = (uint64_t *)(a + oHc);
     }
     KNNG_TRY(cudaMemsetAsync(c->locks, 0, sizeof(int) * nint, c->stream));
     // test hook: the locks of the first h lists start held, so a locked
@@ -335,6 +348,7 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
     c->flags = flags;
     // bf16 tensor-core dots where the contraction is long enough to pay
     c->bf16 = (flags & KNNG_FLAG_BF16) && d >= 64;
+    c->heap = (flags & KNNG_FLAG_HEAP_SAMPLING) != 0;
     c->dpb = (d + 63) & ~63;
     // test hook: run another join kernel the context can use (parity of the
     // three kernels on the same inputs)
@@ -466,7 +480,8 @@ int enqueue_iteration(knng_ctx *c, bool gate) {
     const int li = c->li, it = c->it_done + 1;
     DevState st = c->dev(gate);
     KNNG_TRY(launch_count(st, li, c->stream));
-    KNNG_TRY(launch_sample(st, li, it, c->seed, c->stream));
+    KNNG_TRY(c->heap ? launch_heap_sample(st, li, it, c->seed, c->stream)
+                     : launch_sample(st, li, it, c->seed, c->stream));
     if (c->tune_pending) {
         int rc = autotune_join(c, li);
         if (rc) return rc;
@@ -484,7 +499,7 @@ int enqueue_iteration(knng_ctx *c, bool gate) {
     if (timing) KNNG_TRY(cudaEventRecord(ev[1], c->stream));
     KNNG_TRY(launch_merge(st, li, c->stream));
     if (timing) KNNG_TRY(cudaEventRecord(ev[2], c->stream));
-    c->launches += 3 + join_launches(c->join_path);
+    c->launches += (c->heap ? 5 : 3) + join_launches(c->join_path);
     c->li++;
     c->it_done++;
     if ((c->flags & KNNG_FLAG_REORDER) && !c->reordered && it == 1) {

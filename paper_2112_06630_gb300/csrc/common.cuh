@@ -45,7 +45,7 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
-enum Stream : uint32_t { kStreamInit = 1, kStreamFwd = 2, kStreamRev = 3 };
+enum Stream : uint32_t { kStreamInit = 1, kStreamFwd = 2, kStreamRev = 3, kStreamHeap = 4 };
 __host__ __device__ __forceinline__ uint64_t hash_base(uint64_t seed, uint32_t stream, uint32_t iter) {
     return splitmix64(splitmix64(seed) ^ (((uint64_t)stream << 32) | (uint64_t)iter));
 }
@@ -199,6 +199,11 @@ struct DevState {
     int *fill_new, *fill_old;  // reverse candidate fill counters
     int *fwd_new, *fwd_old;    // accepted forward counts
     int *cand_new, *cand_old;  // n x cap: [0, K) forward part, [K, K + R) reverse part
+    // priority-heap sampling only (else null): each node's reverse offers of
+    // each kind at hcsr[hoff[kind * n + v] ..), claimed from *hcursor
+    int *hoff;                 // 2 x n
+    uint64_t *hcsr;            // n x K keys (priority << 32 | source)
+    int *hcursor;
     long long *stats;
     long long *it_stats;       // (max_iters + 2) x kItCount
     int64_t n;

@@ -17,6 +17,7 @@ cudaError_t launch_init_random(const DevState &st, uint64_t seed, int *err, cuda
 cudaError_t launch_init_graph(const DevState &st, const int32_t *ids, const uint8_t *is_new, int *err,
                               cudaStream_t s);
 cudaError_t launch_count(const DevState &st, int li, cudaStream_t s);
+cudaError_t launch_heap_sample(const DevState &st, int li, int it, uint64_t seed, cudaStream_t s);
 cudaError_t launch_sample(const DevState &st, int li, int it, uint64_t seed, cudaStream_t s);
 cudaError_t launch_join(const DevState &st, int li, cudaStream_t s);
 cudaError_t launch_merge(const DevState &st, int li, cudaStream_t s);

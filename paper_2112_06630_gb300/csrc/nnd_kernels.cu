@@ -153,7 +153,10 @@ __global__ void count_kernel(DevState st, int li) {
         st.fill_new[u] = 0;
         st.fill_old[u] = 0;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *st.pool_next = 0;  // bucket pool restarts
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *st.pool_next = 0;                   // bucket pool restarts
+        if (st.hcursor) *st.hcursor = 0;     // reverse-offer segments restart
+    }
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         if (st.ds && node_skipped(st, e / st.K, li)) continue;
         uint64_t key = st.keys[e];
@@ -224,6 +227,151 @@ cudaError_t launch_sample(const DevState &st, int li, int it, uint64_t seed, cud
     int grid = grid_for((const void *)sample_kernel, kBlock, 0);
     sample_kernel<<<grid, kBlock, 0, s>>>(st, li, hash_base(seed, kStreamFwd, (uint32_t)it),
                                           hash_base(seed, kStreamRev, (uint32_t)it));
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ priority-heap sampling ----
+// The candidate construction of PyNNDescent, the alternative to Section 3.1's
+// turbosampling: edge (u, j) with v = list[u][j] draws one priority
+// p = hi32(h(seed, HEAP, it, u, j)) and offers v to u and u to v, both of the
+// edge's kind (new/old) and with priority p.  Each node keeps per kind the s
+// smallest (priority, id) offers, one per id (its smallest priority).
+//   heap_alloc_kernel   each node's segments for its reverse offers (sizes:
+//                       the count kernel's reverse degrees), claimed from one
+//                       cursor a warp at a time; the layout does not matter,
+//                       the selection is order-independent;
+//   heap_scatter_kernel every edge writes (p << 32 | u) into v's segment;
+//   heap_select_kernel  one warp per node folds its forward entries and its
+//                       reverse offers into two sorted lane lists of s keys,
+//                       writes the kept ids as the forward part of its
+//                       candidates (reverse part empty, old ones that are also
+//                       new dropped) and clears the "new" flag of its forward
+//                       entries kept as new candidates.
+__global__ void __launch_bounds__(256) heap_alloc_kernel(DevState st, int li) {
+    if (iteration_skipped(st, li)) return;
+    const unsigned lane = lane_id();
+    for (long long w = gwarp(); w * 32 < st.n; w += nwarps()) {
+        const long long v = w * 32 + lane;
+        const bool ok = v < st.n;  // nodes of finished data sets have no reverse degree
+        const int cn = ok ? st.rev_new[v] : 0, co = ok ? st.rev_old[v] : 0;
+        int incl = cn + co;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if ((int)lane >= o) incl += t;
+        }
+        int base = 0;
+        if (lane == 31) base = atomicAdd(st.hcursor, incl);
+        base = __shfl_sync(kFull, base, 31);
+        const int start = base + incl - (cn + co);
+        if (ok) {
+            st.hoff[v] = start;
+            st.hoff[st.n + v] = start + cn;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) heap_scatter_kernel(DevState st, int li, uint64_t hbase) {
+    if (iteration_skipped(st, li)) return;
+    const unsigned lane = lane_id();
+    const int K = st.K;
+    long long dropped = 0;
+    for (long long u = gwarp(); u < st.n; u += nwarps()) {
+        if (node_skipped(st, u, li) || (int)lane >= K) continue;
+        const uint64_t key = st.keys[(size_t)u * K + lane];
+        const uint32_t v = key_id(key);
+        const bool isnew = (key & kFlagNew) != 0;
+        const uint32_t p = (uint32_t)(hash_uj(hbase, (uint64_t)node_local(st, u), lane) >> 32);
+        const int slot = atomicAdd(isnew ? &st.fill_new[v] : &st.fill_old[v], 1);
+        if (slot < (isnew ? st.rev_new[v] : st.rev_old[v]))
+            st.hcsr[(size_t)st.hoff[(isnew ? 0 : st.n) + v] + slot] = ((uint64_t)p << 32) | (uint64_t)(uint32_t)u;
+        else
+            ++dropped;  // the segment was sized by the count kernel: cannot happen
+    }
+    dropped = warp_sum(dropped);
+    if (lane == 0 && dropped) atomic_add_ll(&st.stats[kStatRevOverflow], dropped);
+}
+
+// Offer the 32 lanes' keys c (kKeyEmpty = none) to the ascending list S held
+// in lanes 0 .. s-1 (empty above): a key enters if it is among the s smallest;
+// a second offer of an id already listed replaces it only when smaller.
+__device__ __forceinline__ void heap_offer(uint64_t &S, uint64_t c, int s, unsigned lane) {
+    unsigned m = __ballot_sync(kFull, c < __shfl_sync(kFull, S, s - 1));
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const uint64_t x = __shfl_sync(kFull, c, src);
+        const unsigned hit = __ballot_sync(kFull, (int)lane < s && S != kKeyEmpty && (uint32_t)S == (uint32_t)x);
+        if (hit) {
+            const int h = __ffs(hit) - 1;
+            if (x >= __shfl_sync(kFull, S, h)) continue;
+            const uint64_t nxt = __shfl_down_sync(kFull, S, 1);
+            if ((int)lane >= h && (int)lane < s) S = (int)lane == s - 1 ? kKeyEmpty : nxt;
+        } else if (x >= __shfl_sync(kFull, S, s - 1)) {
+            continue;
+        }
+        const int pos = __popc(__ballot_sync(kFull, (int)lane < s && S < x));
+        const uint64_t prv = __shfl_up_sync(kFull, S, 1);
+        if ((int)lane < s) {
+            if ((int)lane == pos) S = x;
+            else if ((int)lane > pos) S = prv;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) heap_select_kernel(DevState st, int li, uint64_t hbase) {
+    if (iteration_skipped(st, li)) return;
+    const unsigned lane = lane_id();
+    const int K = st.K, s = st.s;
+    for (long long x = gwarp(); x < st.n; x += nwarps()) {
+        if (node_skipped(st, x, li)) continue;
+        const bool valid = (int)lane < K;
+        const uint64_t key = valid ? st.keys[(size_t)x * K + lane] : kKeyEmpty;
+        const bool isnew = valid && (key & kFlagNew);
+        const uint32_t p = valid ? (uint32_t)(hash_uj(hbase, (uint64_t)node_local(st, x), lane) >> 32) : 0u;
+        const uint64_t fwd = ((uint64_t)p << 32) | (uint64_t)key_id(key);
+        uint64_t Sn = kKeyEmpty, So = kKeyEmpty;
+        heap_offer(Sn, isnew ? fwd : kKeyEmpty, s, lane);
+        heap_offer(So, valid && !isnew ? fwd : kKeyEmpty, s, lane);
+        for (int f = 0; f < 2; ++f) {
+            const int cnt = min(f ? st.fill_old[x] : st.fill_new[x], f ? st.rev_old[x] : st.rev_new[x]);
+            const size_t off = (size_t)st.hoff[(f ? st.n : 0) + x];
+            for (int b = 0; b < cnt; b += 32) {
+                const uint64_t c = b + (int)lane < cnt ? st.hcsr[off + b + lane] : kKeyEmpty;
+                if (f) heap_offer(So, c, s, lane);
+                else heap_offer(Sn, c, s, lane);
+            }
+        }
+        const size_t cb = (size_t)x * st.cap;
+        const int nn = __popc(__ballot_sync(kFull, Sn != kKeyEmpty));
+        if (Sn != kKeyEmpty) st.cand_new[cb + lane] = (int)(uint32_t)Sn;
+        bool keep_old = So != kKeyEmpty, kept = false;
+        for (int k = 0; k < nn; ++k) {
+            const uint32_t id = (uint32_t)__shfl_sync(kFull, Sn, k);
+            keep_old = keep_old && (uint32_t)So != id;
+            kept = kept || key_id(key) == id;
+        }
+        const unsigned mo = __ballot_sync(kFull, keep_old);
+        if (keep_old) st.cand_old[cb + __popc(mo & lanemask_lt())] = (int)(uint32_t)So;
+        __syncwarp();
+        if (lane == 0) {
+            st.fwd_new[x] = nn;
+            st.fwd_old[x] = __popc(mo);
+            st.fill_new[x] = 0;
+            st.fill_old[x] = 0;
+        }
+        if (valid) {
+            uint64_t nk = key & ~(uint64_t)kFlagIns;
+            if (isnew && kept) nk &= ~(uint64_t)kFlagNew;
+            if (nk != key) st.keys[(size_t)x * K + lane] = nk;
+        }
+    }
+}
+
+cudaError_t launch_heap_sample(const DevState &st, int li, int it, uint64_t seed, cudaStream_t s) {
+    const uint64_t hb = hash_base(seed, kStreamHeap, (uint32_t)it);
+    heap_alloc_kernel<<<grid_for((const void *)heap_alloc_kernel, 256, 0), 256, 0, s>>>(st, li);
+    heap_scatter_kernel<<<grid_for((const void *)heap_scatter_kernel, kBlock, 0), kBlock, 0, s>>>(st, li, hb);
+    heap_select_kernel<<<grid_for((const void *)heap_select_kernel, kBlock, 0), kBlock, 0, s>>>(st, li, hb);
     return cudaGetLastError();
 }
 

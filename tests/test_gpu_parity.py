@@ -511,3 +511,63 @@ def test_autotuned_bf16_and_batched_match_the_oracle():
     for s, (bi, bd) in zip(sets, outs):
         oi, od, _ = oracle.build_knng(s, 10, 0.5, 0.001, 6, seed=2)
         assert (bi.cpu().numpy() == oi).all()
+
+
+# ------------------------------------------------- priority-heap sampling ----
+
+HEAP_CASES = [
+    # n, d, K, rho, int range (ragged warps, s < K and s = K, high reverse degrees)
+    (3001, 8, 10, 0.5, 16),
+    (2500, 16, 20, 0.3, 8),
+    (1200, 17, 32, 1.0, 5),
+    (700, 100, 12, 0.5, 3),
+]
+
+
+@pytest.mark.parametrize("n,d,K,rho,hi", HEAP_CASES)
+def test_heap_sampling_one_iteration_matches_oracle_bit_exact(n, d, K, rho, hi):
+    """KNNG_FLAG_HEAP_SAMPLING from a given graph: the kept candidate sets,
+    the lists, the flags and the counters equal the oracle's priority-heap
+    iteration exactly."""
+    x = _int_data(n, d, hi, seed=n + 7)
+    ids0, new0 = workloads.random_graph(n, K, seed=n + 8, p_new=0.6)
+    with knng.Context(_cuda(x), K, rho=rho, seed=13, graph=(ids0, new0), iter=0,
+                      flags=knng.FLAG_HEAP_SAMPLING) as c:
+        conv, ch = c.iterate()
+        gnew, gold = c.samples()
+        gi, gd, gf = c.state()
+        stats = c.stats()
+    st = oracle.State(x, K, rho, seed=13, sampler="heap")
+    st.init_graph(ids0, new0, 0)
+    r = st.iterate()
+    s = oracle.sample_size(rho, K)
+    onew, oold = st.samples()
+    assert stats["rev_overflow"] == 0 and stats["set_overflow"] == 0
+    for u in range(n):
+        assert len(gnew[u]) <= s and len(gold[u]) <= s
+        assert set(gnew[u].tolist()) == set(onew[u].tolist())
+        assert set(gold[u].tolist()) == set(oold[u].tolist())
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    assert ch == r["changes"] and stats["dist_evals"] == r["evals"]
+
+
+@pytest.mark.parametrize("flags", [0, knng.FLAG_GRAPH])
+def test_heap_sampling_build_matches_oracle_bit_exact(flags):
+    n, d, K = 4000, 6, 16
+    x = _int_data(n, d, 9, seed=31)
+    gi, gd, st = knng.knng_build(_cuda(x), K, rho=0.5, delta=0.001, max_iters=12, seed=6,
+                                 flags=knng.FLAG_HEAP_SAMPLING | flags)
+    oi, od, ost = oracle.build_knng(x, K, 0.5, 0.001, 12, seed=6, sampler="heap")
+    assert st["iterations"] == ost["iters"] and st["dist_evals"] == ost["evals"]
+    assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+def test_heap_sampling_batched_matches_oracle_per_data_set():
+    sets = [_int_data(n, d, 6, seed=200 + n) for n, d in [(700, 8), (1500, 3), (400, 96), (60, 5)]]
+    K, rho, delta, iters = 8, 0.5, 0.002, 8
+    outs, _ = knng.knng_build_batched([_cuda(x) for x in sets], K, rho, delta, iters, seed=5,
+                                      flags=knng.FLAG_HEAP_SAMPLING)
+    for x, (gi, gd) in zip(sets, outs):
+        oi, od, _ = oracle.build_knng(x, K, rho, delta, iters, seed=5, sampler="heap")
+        assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
