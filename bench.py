@@ -452,7 +452,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     flags = (knng.FLAG_REORDER if args.reorder else 0) | (knng.FLAG_BF16 if args.bf16 else 0) | \
-        (knng.FLAG_GRAPH if args.graph else 0) | (knng.FLAG_AUTOTUNE if args.autotune else 0)
+        (knng.FLAG_GRAPH if args.graph else 0) | (knng.FLAG_AUTOTUNE if args.autotune else 0) | \
+        (knng.FLAG_HEAP_SAMPLING if args.heap else 0)
     dp = (w.d + 3) // 4 * 4
     if args.bf16 and w.d >= 64:
         dp = (w.d + 63) // 64 * 64 // 2  # bf16 rows: half the bytes of float32
@@ -515,6 +516,33 @@ def run_gpu(args):
     bi, _ = knng.knng_bruteforce(xd, w.K, rows=torch.from_numpy(rows).to(device))
     rec = metrics.recall(x, ids.cpu().numpy(), bi.cpu().numpy(), rows)
 
+    # the metric's recall condition: when the stated sample rate stops short
+    # of recall 0.99, the smallest larger rate of a short ladder that reaches
+    # it, timed the same way (same rows, same flush, same step count)
+    at99 = None
+    if rec < 0.99 and not args.rho:
+        for r in (0.6, 0.7, 0.8, 1.0):
+            if r <= w.rho:
+                continue
+            for _ in range(args.warmup):
+                knng.knng_build(xd, w.K, r, w.delta, w.max_iters, seed=0, flags=flags)
+            ts = []
+            for _ in range(args.steps):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                s0 = torch.cuda.Event(enable_timing=True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                ri, _, rst = knng.knng_build(xd, w.K, r, w.delta, w.max_iters, seed=0, flags=flags)
+                e0.record(stream)
+                torch.cuda.synchronize()
+                ts.append(s0.elapsed_time(e0) / 1e3)
+            rr = metrics.recall(x, ri.cpu().numpy(), bi.cpu().numpy(), rows)
+            if rr >= 0.99:
+                at99 = {"rho": r, "s": rst["s"], "value": round(sum(ts) / len(ts), 6), "unit": "s",
+                        "recall_at_k": round(rr, 5), "iterations": rst["iterations"]}
+                break
+
     peaks = _peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     ran = max(1, tst["join_ran"])
@@ -544,10 +572,13 @@ def run_gpu(args):
         "config": {"workload": wname, "n": w.n, "d": w.d, "K": w.K, "rho": w.rho, "delta": w.delta,
                    "max_iters": w.max_iters, "reorder": bool(args.reorder), "bf16": bool(args.bf16),
                    "graph": bool(args.graph), "autotune": bool(args.autotune), "join_path": stats["join_path"],
+                   "sampler": "heap" if args.heap else "turbo",
                    "parallelism": f"replicas{ws}",
                    "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
         "recall_at_k": round(rec, 5), "recall_rows": RECALL_ROWS,
+        "at_recall_0.99": at99,
         "iterations": stats["iterations"], "dist_evals": stats["dist_evals"],
+        "selection_ms_per_iter": round(tst["sample_ms_ran"] / ran, 4),
         "dist_evals_per_s": round(stats["dist_evals"] / (step_s), 1),
         "paper_flops_per_s": round(stats["dist_evals"] * (3 * w.d - 1) / step_s, 1),
         "e2e": {"value": round(e2e_s / n_builds, 6), "unit": "s", "h2d_bytes_per_step": int(x.nbytes),
@@ -623,6 +654,8 @@ def main():
     ap.add_argument("--bf16", action="store_true", help="bf16 tensor-core dots for d >= 64, float32 re-rank")
     ap.add_argument("--graph", action="store_true", help="launch the iteration loop as one captured CUDA graph")
     ap.add_argument("--autotune", action="store_true", help="time the join kernels on the first build, keep the fastest")
+    ap.add_argument("--heap", action="store_true",
+                    help="priority-heap candidate selection instead of Section 3.1's turbosampling")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["batched_256"],
                     help="another workload than the headline one (measurement table)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")

@@ -98,6 +98,8 @@ typedef struct knng_stats {
                                   floats), 1 block-per-node tiles, 2 TMA-staged ring */
     double join_ms_ran;        /* summed join-kernel time of those iterations */
     double merge_ms_ran;       /* summed list-merge-kernel time of those iterations */
+    double sample_ms_ran;      /* summed selection-step time (degree count + sampling kernels) of
+                                  those iterations (KNNG_FLAG_TIMING) */
 } knng_stats;
 
 /*

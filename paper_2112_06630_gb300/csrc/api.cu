@@ -146,7 +146,8 @@ struct knng_ctx {
     std::vector<cudaGraphExec_t> graphs;  // captured iteration loops (KNNG_FLAG_GRAPH)
     cudaStream_t capture = nullptr;       // private stream the loops are captured on
 
-    std::vector<cudaEvent_t> ev;  // start/stop pairs around join launches
+    std::vector<cudaEvent_t> ev;  // per timed iteration: before count, after sampling, before join,
+                                  // after join, after merge
     std::vector<int> ev_li;       // iteration index of each pair
 
     DevState dev(bool gate) const {
@@ -479,26 +480,28 @@ int enqueue_iteration(knng_ctx *c, bool gate) {
     if (c->li >= kMaxLocalIters) return KNNG_ERR_STATE;
     const int li = c->li, it = c->it_done + 1;
     DevState st = c->dev(gate);
-    KNNG_TRY(launch_count(st, li, c->stream));
-    KNNG_TRY(c->heap ? launch_heap_sample(st, li, it, c->seed, c->stream)
-                     : launch_sample(st, li, it, c->seed, c->stream));
-    if (c->tune_pending) {
-        int rc = autotune_join(c, li);
-        if (rc) return rc;
-        st = c->dev(gate);
-    }
     const bool timing = (c->flags & KNNG_FLAG_TIMING) != 0;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     if (timing) {
         for (auto &e : ev) KNNG_TRY(cudaEventCreate(&e));
         for (auto &e : ev) c->ev.push_back(e);
         c->ev_li.push_back(li);
         KNNG_TRY(cudaEventRecord(ev[0], c->stream));
     }
-    KNNG_TRY(launch_join(st, li, c->stream));
+    KNNG_TRY(launch_count(st, li, c->stream));
+    KNNG_TRY(c->heap ? launch_heap_sample(st, li, it, c->seed, c->stream)
+                     : launch_sample(st, li, it, c->seed, c->stream));
     if (timing) KNNG_TRY(cudaEventRecord(ev[1], c->stream));
-    KNNG_TRY(launch_merge(st, li, c->stream));
+    if (c->tune_pending) {
+        int rc = autotune_join(c, li);
+        if (rc) return rc;
+        st = c->dev(gate);
+    }
     if (timing) KNNG_TRY(cudaEventRecord(ev[2], c->stream));
+    KNNG_TRY(launch_join(st, li, c->stream));
+    if (timing) KNNG_TRY(cudaEventRecord(ev[3], c->stream));
+    KNNG_TRY(launch_merge(st, li, c->stream));
+    if (timing) KNNG_TRY(cudaEventRecord(ev[4], c->stream));
     c->launches += (c->heap ? 5 : 3) + join_launches(c->join_path);
     c->li++;
     c->it_done++;
@@ -775,13 +778,16 @@ int knng_get_stats(knng_ctx *c, knng_stats *out) {
     out->join_ms = 0;
     out->join_ms_ran = 0;
     out->merge_ms_ran = 0;
-    for (size_t i = 0; i + 2 < c->ev.size(); i += 3) {
-        float ms = 0, ms2 = 0;
-        if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess &&
-            cudaEventElapsedTime(&ms2, c->ev[i + 1], c->ev[i + 2]) == cudaSuccess) {
+    out->sample_ms_ran = 0;
+    for (size_t i = 0; i + 4 < c->ev.size(); i += 5) {
+        float ms0 = 0, ms = 0, ms2 = 0;
+        if (cudaEventElapsedTime(&ms0, c->ev[i], c->ev[i + 1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, c->ev[i + 2], c->ev[i + 3]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms2, c->ev[i + 3], c->ev[i + 4]) == cudaSuccess) {
             out->join_ms += ms;
             out->join_launches++;
-            if (its[(size_t)c->ev_li[i / 3] * kItCount + kItRan]) {
+            if (its[(size_t)c->ev_li[i / 5] * kItCount + kItRan]) {
+                out->sample_ms_ran += ms0;
                 out->join_ms_ran += ms;
                 out->merge_ms_ran += ms2;
                 out->join_ran++;
@@ -971,6 +977,7 @@ void add_stats(knng_stats &a, const knng_stats &b) {
     a.join_path = b.join_path;
     a.join_ms_ran += b.join_ms_ran;
     a.merge_ms_ran += b.merge_ms_ran;
+    a.sample_ms_ran += b.sample_ms_ran;
 }
 
 }  // namespace

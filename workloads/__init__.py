@@ -211,6 +211,9 @@ WORKLOADS = {
     # MNIST-shaped integer data
     "mnist_like_n70k_d784": Workload("mnist_like_n70k_d784", 70_000, 784, 20, 0.5, 0.001, 15,
                                      "mnist_like"),
+    # the selection-step comparison setting: Single Gaussian, covariance 2 I
+    "gaussian_n16k_d8": Workload("gaussian_n16k_d8", 16_384, 8, 20, 0.5, 0.001, 15, "single_gaussian",
+                                 (("var", 2.0),)),
     # Audio-shaped: 54,387 x 192 frames of 500 smooth utterances
     "audio_like_n54k_d192": Workload("audio_like_n54k_d192", 54_387, 192, 20, 0.5, 0.001, 15, "audio_like"),
     # large dense, 1000 clusters, centres N(0, 4I), sigma 0.5
