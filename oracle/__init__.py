@@ -64,6 +64,7 @@ def _load():
             "orc_get_sigma": (i32, [P, P]),
             "orc_free": (None, [P]),
             "orc_greedy_reorder": (i32, [P, i64, i32, i32, P, P]),
+            "orc_parallel_relabel": (i32, [P, i64, i32, i32, P, i32, P, P, P, P]),
             "orc_build": (i32, [P, i64, i32, i32, f32, f32, i32, u64, i32, i32, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -129,6 +130,25 @@ def greedy_reorder(lists, reading_b: bool = False):
     si = np.empty(n, np.int32)
     _load().orc_greedy_reorder(_p(lists), n, K, int(reading_b), _p(sg), _p(si))
     return sg, si
+
+
+def parallel_relabel(data, lists, rmax: int = 64):
+    """Parallel relabelling variant (single-linkage Boruvka rounds on the list
+    graph).  Returns (levels (R, n) int32: each round's component
+    representatives, msf_weight, sigma (n,) int32 with every component of
+    every round contiguous)."""
+    data = _f32(data)
+    lists = np.ascontiguousarray(lists, dtype=np.int32)
+    n, K = lists.shape
+    levels = np.empty((rmax, n), np.int32)
+    rounds = ctypes.c_int(0)
+    w = ctypes.c_double(0.0)
+    sg = np.empty(n, np.int32)
+    rc = _load().orc_parallel_relabel(_p(data), n, data.shape[1], K, _p(lists), rmax, _p(levels),
+                                      ctypes.byref(rounds), ctypes.byref(w), _p(sg))
+    if rc:
+        raise MemoryError("orc_parallel_relabel")
+    return levels[:rounds.value].copy(), float(w.value), sg
 
 
 def build_knng(data, K: int, rho: float, delta: float, max_iters: int, seed: int = 0,

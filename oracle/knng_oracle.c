@@ -682,6 +682,132 @@ int orc_greedy_reorder(const int32_t *lists, int64_t n, int K, int reading_b,
  * Move every node u to spot sigma(u) at once (Section 3.2): its point, its
  * list (ids renamed through sigma, re-sorted by (dist, new id)).
  */
+/*
+ * Parallel relabelling variant (a data-parallel alternative to Algorithm 1,
+ * Section 3.2): single-linkage agglomeration by Boruvka rounds on the graph of
+ * the lists.  Edges are the list entries {u, v}, undirected, ordered by
+ * (float32 distance, min(u, v), max(u, v)).  Each round every component picks
+ * its smallest outgoing edge and hooks onto the component at its other end;
+ * where two components picked the same edge the one with the smaller
+ * representative stays the root; every component then takes the
+ * representative at the end of its hooks.  Rounds stop when no component has
+ * an outgoing edge (or after rmax).
+ *
+ * levels[r * n + u] = representative of u's component after round r, for
+ * r < *rounds.  weight = total distance of the hooked edges (each counted
+ * once): a minimum spanning forest of the list graph.  sigma[u] = spot of u
+ * in the layout that sorts points by (levels[R-1], ..., levels[0], u): every
+ * component of every round is one contiguous range.
+ */
+static const int32_t *orc_lv;
+static int64_t orc_lv_n;
+static int orc_lv_r;
+
+static int orc_cmp_levels(const void *pa, const void *pb)
+{
+    int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
+    for (int r = orc_lv_r - 1; r >= 0; --r) {
+        int32_t x = orc_lv[(int64_t)r * orc_lv_n + a], y = orc_lv[(int64_t)r * orc_lv_n + b];
+        if (x != y) return x < y ? -1 : 1;
+    }
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+int orc_parallel_relabel(const float *data, int64_t n, int d, int K, const int32_t *ids, int rmax,
+                         int32_t *levels, int *rounds, double *weight, int32_t *sigma)
+{
+    int32_t *comp = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *broke = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    uint64_t *best1 = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    uint32_t *best2 = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    float *dist = (float *)malloc(sizeof(float) * (size_t)n * (size_t)K);
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!comp || !parent || !broke || !best1 || !best2 || !dist || !order) {
+        free(comp); free(parent); free(broke); free(best1); free(best2); free(dist); free(order);
+        return -2;
+    }
+    for (int64_t u = 0; u < n; ++u) {
+        comp[u] = (int32_t)u;
+        for (int k = 0; k < K; ++k) dist[u * K + k] = orc_dist32(data, d, u, ids[u * K + k]);
+    }
+    double w = 0.0;
+    int r = 0;
+    for (; r < rmax; ++r) {
+        for (int64_t c = 0; c < n; ++c) {
+            best1[c] = UINT64_MAX;
+            best2[c] = UINT32_MAX;
+        }
+        for (int pass = 0; pass < 2; ++pass)
+            for (int64_t u = 0; u < n; ++u)
+                for (int k = 0; k < K; ++k) {
+                    uint32_t v = (uint32_t)ids[u * K + k], uu = (uint32_t)u;
+                    int32_t cu = comp[u], cv = comp[v];
+                    if (cu == cv) continue;
+                    uint32_t bits;
+                    memcpy(&bits, &dist[u * K + k], sizeof(bits));
+                    uint64_t k1 = ((uint64_t)bits << 32) | (uint64_t)(uu < v ? uu : v);
+                    uint32_t mx = uu < v ? v : uu;
+                    if (pass == 0) {
+                        if (k1 < best1[cu]) best1[cu] = k1;
+                        if (k1 < best1[cv]) best1[cv] = k1;
+                    } else {
+                        if (best1[cu] == k1 && mx < best2[cu]) best2[cu] = mx;
+                        if (best1[cv] == k1 && mx < best2[cv]) best2[cv] = mx;
+                    }
+                }
+        int64_t hooks = 0;
+        for (int64_t c = 0; c < n; ++c) {
+            if (comp[c] != (int32_t)c) continue;
+            if (best1[c] == UINT64_MAX) {
+                parent[c] = (int32_t)c;
+                continue;
+            }
+            uint32_t a = (uint32_t)best1[c], b = best2[c];
+            uint32_t other = comp[a] == (int32_t)c ? b : a;
+            parent[c] = comp[other];
+            ++hooks;
+        }
+        if (hooks == 0) break;
+        /* 2-cycles: the smaller representative stays the root */
+        for (int64_t c = 0; c < n; ++c) broke[c] = 0;
+        for (int64_t c = 0; c < n; ++c) {
+            if (comp[c] != (int32_t)c) continue;
+            int32_t p = parent[c];
+            if (p != (int32_t)c && parent[p] == (int32_t)c && (int32_t)c < p) broke[c] = 1;
+        }
+        for (int64_t c = 0; c < n; ++c) {
+            if (comp[c] != (int32_t)c) continue;
+            if (broke[c]) parent[c] = (int32_t)c;
+            if (parent[c] != (int32_t)c) {
+                float f;
+                uint32_t bits = (uint32_t)(best1[c] >> 32);
+                memcpy(&f, &bits, sizeof(f));
+                w += (double)f;
+            }
+        }
+        for (int64_t u = 0; u < n; ++u) {
+            int32_t x = comp[u];
+            while (parent[x] != x) x = parent[x];
+            order[u] = x;
+        }
+        for (int64_t u = 0; u < n; ++u) {
+            comp[u] = order[u];
+            levels[(int64_t)r * n + u] = comp[u];
+        }
+    }
+    *rounds = r;
+    if (weight) *weight = w;
+    for (int64_t u = 0; u < n; ++u) order[u] = (int32_t)u;
+    orc_lv = levels;
+    orc_lv_n = n;
+    orc_lv_r = r;
+    qsort(order, (size_t)n, sizeof(int32_t), orc_cmp_levels);
+    for (int64_t i = 0; i < n; ++i) sigma[order[i]] = (int32_t)i;
+    free(comp); free(parent); free(broke); free(best1); free(best2); free(dist); free(order);
+    return 0;
+}
+
 static int orc_apply_permutation(orc_state *st, const int32_t *sigma)
 {
     int64_t n = st->n;

@@ -471,6 +471,70 @@ def test_alg1_recovers_clusters_early():
     assert lit[:half].mean() < after[:half].mean()
 
 
+# ------------------------------------------- parallel relabelling variant ----
+
+def _contiguous(levels, sigma):
+    """Every component of every round occupies one contiguous range of spots."""
+    for lv in levels:
+        order = np.argsort(lv, kind="stable")
+        lab = lv[order]
+        pos = sigma[order]
+        cut = np.flatnonzero(np.diff(lab)) + 1
+        for seg in np.split(pos, cut):
+            if seg.max() - seg.min() + 1 != len(seg):
+                return False
+    return True
+
+
+@pytest.mark.parametrize("n,K,seed", [(300, 4, 1), (2000, 6, 2), (5000, 3, 3)])
+def test_parallel_relabel_is_single_linkage(n, K, seed):
+    """The hooked edges form a minimum spanning forest of the list graph
+    (single linkage): same total weight and same components as scipy's
+    minimum_spanning_tree / connected_components on the symmetrised graph."""
+    sp = pytest.importorskip("scipy.sparse")
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    x = workloads.uniform(n, 3, seed)
+    ids, _ = workloads.random_graph(n, K, seed=seed + 10, p_new=1.0)
+    levels, w, sg = oracle.parallel_relabel(x, ids)
+    rows = np.repeat(np.arange(n), K)
+    cols = ids.ravel()
+    x64 = x.astype(np.float64)
+    wt = np.array([np.float32(((x64[a] - x64[b]) ** 2).sum()) for a, b in zip(rows, cols)], np.float64)
+    g = sp.coo_matrix((wt, (rows, cols)), shape=(n, n)).tocsr()
+    g = g.maximum(g.T)
+    mst = csgraph.minimum_spanning_tree(g)
+    assert abs(w - mst.sum()) <= 1e-9 * max(1.0, mst.sum())
+    ncomp, _ = csgraph.connected_components(g, directed=False)
+    assert len(np.unique(levels[-1])) == ncomp
+    assert sorted(sg.tolist()) == list(range(n))
+    assert _contiguous(levels, sg)
+
+
+def test_parallel_relabel_recovers_clusters_everywhere():
+    """Fig. 4 setting (clustered, n = 16,384, d = 8, 8 clusters; lists after
+    one iteration, windows of 2,000): single linkage merges the clusters last,
+    so every cluster is one run of spots -- every window holds at most two
+    clusters -- where Algorithm 1's tail falls towards 1/c."""
+    n, d, c = 16384, 8, 8
+    x, lab = workloads.gaussian_mixture(n, d, c, seed=2, return_labels=True)
+    st = oracle.State(x, 20, 0.5, seed=1)
+    st.init_random()
+    st.iterate()
+    ids, _, _ = st.state()
+    levels, _, sg = oracle.parallel_relabel(x, ids)
+    inv = np.empty(n, np.int64)
+    inv[sg] = np.arange(n)
+    par = metrics.window_purity(lab[inv], 2000, c)
+    runs = (np.diff(lab[inv]) != 0).sum() + 1
+    assert runs == c
+    a1, _ = oracle.greedy_reorder(ids)
+    inv1 = np.empty(n, np.int64)
+    inv1[a1] = np.arange(n)
+    alg1 = metrics.window_purity(lab[inv1], 2000, c)
+    assert par.min() >= 0.8 and par.mean() > alg1.mean()
+    assert _contiguous(levels, sg)
+
+
 def test_build_with_reorder_returns_original_labels():
     w, x = workloads.make("uniform_n2k_d8")
     ei, _ = oracle.bruteforce(x, w.K)
