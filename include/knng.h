@@ -69,6 +69,12 @@ extern "C" {
                                         u, u to v, of the edge's new/old kind); each node keeps per kind
                                         the s smallest (priority, id) offers, one per id; forward new
                                         entries kept as new candidates lose their flag */
+#define KNNG_FLAG_REORDER_PARALLEL 0x80u /* with REORDER: relabel by the data-parallel variant instead of
+                                           Algorithm 1 -- single-linkage (Boruvka) rounds on the list graph,
+                                           edges ordered by (float32 distance, min id, max id), every
+                                           component of every round laid out in one contiguous range of
+                                           spots; the order of siblings inside a parent's range comes from
+                                           atomics, so it is not reproducible run to run */
 
 typedef struct knng_ctx knng_ctx;
 

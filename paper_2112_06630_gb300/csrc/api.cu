@@ -123,6 +123,7 @@ struct knng_ctx {
     uint64_t *keys = nullptr, *keys2 = nullptr;
     int *locks = nullptr, *ibuf = nullptr, *cand = nullptr, *err = nullptr, *pcursor = nullptr;
     bool heap = false;  // KNNG_FLAG_HEAP_SAMPLING
+    unsigned char *rscratch = nullptr;  // KNNG_FLAG_REORDER_PARALLEL scratch
     int *hoff = nullptr, *hcursor = nullptr;
     uint64_t *hcsr = nullptr;
     int *pchunk = nullptr, *pool_next = nullptr;
@@ -242,6 +243,8 @@ int ctx_alloc(knng_ctx *c) {
                       (c->tune_pending && ring_join_fits(c->bf16, c->nv, c->dpb, c->K));
     const size_t oCs = ring ? take(sizeof(int) * (size_t)n * kSetMax) : 0;
     const size_t oCm = ring ? take(sizeof(int) * (size_t)n) : 0;
+    const bool prel = reorder && (c->flags & KNNG_FLAG_REORDER_PARALLEL);
+    const size_t oR = prel ? take(parallel_relabel_scratch(n, c->K)) : 0;
     const size_t oHo = c->heap ? take(sizeof(int) * (2 * (size_t)n + 1)) : 0;
     const size_t oHc = c->heap ? take(sizeof(uint64_t) * (size_t)n * c->K) : 0;
     cudaError_t e = lib_malloc((void **)&c->arena, off, c->stream);
@@ -280,6 +283,7 @@ int ctx_alloc(knng_ctx *c) {
         c->cset = (int *)(a + oCs);
         c->cmeta = (int *)(a + oCm);
     }
+    if (prel) c->rscratch = a + oR;
     if (c->heap) {
         c->hoff = (int *)(a + oHo);
         c->hcursor = c->hoff + 2 * n;
@@ -400,11 +404,18 @@ int ctx_check(knng_ctx *c) {
 
 int enqueue_reorder(knng_ctx *c) {
     if (!c->sigma) return KNNG_ERR_STATE;
-    const int reading_b = (c->flags & KNNG_FLAG_REORDER_B) ? 1 : 0;
-    KNNG_TRY(launch_greedy_reorder(c->keys, c->n, c->K, reading_b, c->sigma, c->sigma_inv, c->stream));
+    if (c->rscratch) {
+        int nl = 0;
+        KNNG_TRY(launch_parallel_relabel(c->X, c->keys, c->n, c->K, c->nv, c->sigma, c->rscratch, &nl, c->stream));
+        c->launches += nl;
+    } else {
+        const int reading_b = (c->flags & KNNG_FLAG_REORDER_B) ? 1 : 0;
+        KNNG_TRY(launch_greedy_reorder(c->keys, c->n, c->K, reading_b, c->sigma, c->sigma_inv, c->stream));
+        c->launches++;
+    }
     DevState st = c->dev(false);
     KNNG_TRY(launch_permute(st, c->X2, c->keys2, c->sigma, c->total_perm, c->stream));
-    c->launches += 2;
+    c->launches++;
     std::swap(c->X, c->X2);
     std::swap(c->keys, c->keys2);
     if (c->bf16) {

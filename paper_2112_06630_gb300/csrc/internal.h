@@ -17,6 +17,11 @@ cudaError_t launch_init_random(const DevState &st, uint64_t seed, int *err, cuda
 cudaError_t launch_init_graph(const DevState &st, const int32_t *ids, const uint8_t *is_new, int *err,
                               cudaStream_t s);
 cudaError_t launch_count(const DevState &st, int li, cudaStream_t s);
+// parallel locality relabelling (relabel.cu): scratch bytes, and the launch
+// that writes sigma (new spot of every node) from the current lists
+size_t parallel_relabel_scratch(int64_t n, int K);
+cudaError_t launch_parallel_relabel(const float *X, const uint64_t *keys, int64_t n, int K, int nv, int32_t *sigma,
+                                    unsigned char *scratch, int *launches, cudaStream_t s);
 cudaError_t launch_heap_sample(const DevState &st, int li, int it, uint64_t seed, cudaStream_t s);
 cudaError_t launch_sample(const DevState &st, int li, int it, uint64_t seed, cudaStream_t s);
 cudaError_t launch_join(const DevState &st, int li, cudaStream_t s);

@@ -571,3 +571,66 @@ def test_heap_sampling_batched_matches_oracle_per_data_set():
     for x, (gi, gd) in zip(sets, outs):
         oi, od, _ = oracle.build_knng(x, K, rho, delta, iters, seed=5, sampler="heap")
         assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+# ------------------------------------------- parallel relabelling variant ----
+
+def _contiguous(levels, sigma):
+    for lv in levels:
+        order = np.argsort(lv, kind="stable")
+        pos = sigma[order]
+        for seg in np.split(pos, np.flatnonzero(np.diff(lv[order])) + 1):
+            if seg.max() - seg.min() + 1 != len(seg):
+                return False
+    return True
+
+
+@pytest.mark.parametrize("n,d,K,hi", [(3000, 4, 8, 6), (20000, 8, 16, 5), (777, 17, 5, 3)])
+def test_parallel_relabel_matches_oracle_hierarchy(n, d, K, hi):
+    """KNNG_FLAG_REORDER_PARALLEL on given lists (integer data, so the float32
+    distances and their ties equal the oracle's): sigma is a permutation in
+    which every component of every round of the oracle's single-linkage
+    hierarchy is contiguous, and the lists moved to their new spots."""
+    x = _int_data(n, d, hi, seed=n + 3)
+    ids0, new0 = workloads.random_graph(n, K, seed=n + 4, p_new=1.0)
+    flags = knng.FLAG_REORDER | knng.FLAG_REORDER_PARALLEL
+    with knng.Context(_cuda(x), K, rho=1.0, flags=flags, graph=(ids0, new0)) as c:
+        c.reorder()
+        sg = c.permutation()
+        gi, _, _ = c.state()
+    levels, _, _ = oracle.parallel_relabel(x, ids0)
+    assert sorted(sg.tolist()) == list(range(n))
+    assert _contiguous(levels, sg)
+    ri = sg[ids0]
+    for u in range(0, n, 37):
+        assert set(gi[sg[u]].tolist()) == set(ri[u].tolist())
+
+
+def test_parallel_relabel_builds_and_periodic_relabels():
+    """Whole builds with the parallel variant after iteration 1 reach the
+    plain build's recall (within 0.005), and relabelling again every two
+    iterations through the step API keeps a valid graph in the caller's
+    labels."""
+    x, lab = workloads.gaussian_mixture(30000, 16, 20, seed=8, return_labels=True)
+    K = 16
+    rows = np.random.default_rng(0).choice(len(x), 1500, replace=False)
+    ei, _ = knng.knng_bruteforce(_cuda(x), K, rows=torch.from_numpy(rows).cuda())
+    ei = ei.cpu().numpy()
+    pi, pd, _ = knng.knng_build(_cuda(x), K, 0.5, 0.001, 12, seed=3)
+    flags = knng.FLAG_REORDER | knng.FLAG_REORDER_PARALLEL
+    ri, rd, st = knng.knng_build(_cuda(x), K, 0.5, 0.001, 12, seed=3, flags=flags)
+    assert st["reordered"] == 1
+    rp = metrics.recall(x, pi.cpu().numpy(), ei, rows)
+    rr = metrics.recall(x, ri.cpu().numpy(), ei, rows)
+    assert rr >= rp - 0.005
+    assert metrics.check_graph(x, ri.cpu().numpy(), rd.cpu().numpy()) == []
+    with knng.Context(_cuda(x), K, rho=0.5, seed=3, flags=flags) as c:
+        for it in range(8):
+            c.iterate()
+            if it % 2 == 1:
+                c.reorder()
+        gi, gd = c.get(device=False)
+        sg = c.permutation()
+    assert sorted(sg.tolist()) == list(range(len(x)))
+    assert metrics.check_graph(x, gi, gd) == []
+    assert metrics.recall(x, gi, ei, rows) >= rp - 0.01
