@@ -434,6 +434,73 @@ def run_bruteforce(args):
     print(json.dumps(line), flush=True)
 
 
+def run_relabel_ab(args):
+    """Relabelling after iteration 1 (Section 3.2): none, Algorithm 1 (exact,
+    sequential) and the parallel single-linkage variant.  One JSON line per
+    workload and variant: build time (CUDA events, L2 flushed), the
+    relabelling's own time (events around it), local-join time per running
+    iteration, recall on 2,000 sampled rows, and the window purity of the
+    layout -- the Fig. 4 measure: the fraction of the most frequent cluster
+    in each window of 2,000 spots."""
+    import numpy as np
+    import torch
+
+    import paper_2112_06630_gb300 as knng
+    from oracle import metrics
+
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    cases = [
+        # name, n, d, K, rho, delta, iterations, mixture parameters (Fig. 4: 8 clusters)
+        ("clustered_n16k_d8_c8", 16384, 8, 20, 0.5, 0.001, 15, dict(clusters=8)),
+        ("clustered_n100k_d16", 100_000, 16, 20, 0.5, 0.001, 15, dict(clusters=50)),
+        ("mixture_n1m_d128", 1_000_000, 128, 32, 0.3, 0.001, 12, dict(clusters=1000, centre_std=2.0, sigma=0.5)),
+    ]
+    variants = [("none", 0), ("algorithm1", knng.FLAG_REORDER),
+                ("parallel", knng.FLAG_REORDER | knng.FLAG_REORDER_PARALLEL)]
+    for name, n, d, K, rho, delta, iters, mp in cases:
+        x, lab = workloads.gaussian_mixture(n, d, seed=0, return_labels=True, **mp)
+        xd = torch.from_numpy(x).to(device)
+        rows = np.random.default_rng(0).choice(n, RECALL_ROWS, replace=False)
+        ei, _ = knng.knng_bruteforce(xd, K, rows=torch.from_numpy(rows).to(device))
+        ei = ei.cpu().numpy()
+        nclu = int(lab.max()) + 1
+        for vname, flags in variants:
+            steps = args.steps if not (vname == "algorithm1" and n > 200_000) else min(args.steps, 2)
+            for _ in range(min(args.warmup, 2) if steps < args.steps else args.warmup):
+                knng.knng_build(xd, K, rho, delta, iters, seed=0, flags=flags)
+            ts = []
+            for _ in range(steps):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                s0 = torch.cuda.Event(enable_timing=True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                s0.record()
+                knng.knng_build(xd, K, rho, delta, iters, seed=0, flags=flags)
+                e0.record()
+                torch.cuda.synchronize()
+                ts.append(s0.elapsed_time(e0) / 1e3)
+            with knng.Context(xd, K, rho=rho, delta=delta, seed=0, flags=flags | knng.FLAG_TIMING) as c:
+                c.run(iters)
+                st = c.stats()
+                sg = c.permutation()
+                gi, _ = c.get(device=False)
+            inv = np.empty(n, np.int64)
+            inv[sg] = np.arange(n)
+            pur = metrics.window_purity(lab[inv], 2000, nclu)
+            ran = max(1, st["join_ran"])
+            print(json.dumps({
+                "relabel": vname, "workload": name, "n": n, "d": d, "K": K, "clusters": nclu,
+                "build_s": round(sum(ts) / len(ts), 6), "steps": steps,
+                "relabel_ms": round(st["reorder_ms"], 3), "iterations": st["iterations"],
+                "join_ms_per_iter": round(st["join_ms_ran"] / ran, 4),
+                "recall_at_k": round(metrics.recall(x, gi, ei, rows), 5),
+                "window_purity": {"windows": len(pur), "mean": round(float(pur.mean()), 4),
+                                  "min": round(float(pur.min()), 4), "last": round(float(pur[-1]), 4)},
+            }), flush=True)
+
+
 def run_gpu(args):
     import torch
 
@@ -662,6 +729,8 @@ def main():
     ap.add_argument("--sweep-d", action="store_true", help="dimension sweep at n=16,384 (one JSON line per run)")
     ap.add_argument("--bruteforce", action="store_true", help="time the exact brute-force K-NNG on the workload")
     ap.add_argument("--rows", type=int, default=0, help="brute force: sampled query rows (0 = every row)")
+    ap.add_argument("--relabel-ab", action="store_true",
+                    help="no relabelling vs Algorithm 1 vs the parallel variant (one JSON line each)")
     ap.add_argument("--n", type=int, default=None, help="override the workload's point count (profiling)")
     ap.add_argument("--rho", type=float, default=None, help="override the sample rate (recall sweeps)")
     ap.add_argument("--delta", type=float, default=None, help="override the termination threshold")
@@ -674,6 +743,8 @@ def main():
         run_sweep(args)
     elif args.bruteforce and args.impl == "gb300":
         run_bruteforce(args)
+    elif args.relabel_ab and args.impl == "gb300":
+        run_relabel_ab(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched_256":

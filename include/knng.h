@@ -106,6 +106,8 @@ typedef struct knng_stats {
     double merge_ms_ran;       /* summed list-merge-kernel time of those iterations */
     double sample_ms_ran;      /* summed selection-step time (degree count + sampling kernels) of
                                   those iterations (KNNG_FLAG_TIMING) */
+    double reorder_ms;         /* summed relabelling time, permutation of rows and lists included
+                                  (KNNG_FLAG_TIMING) */
 } knng_stats;
 
 /*

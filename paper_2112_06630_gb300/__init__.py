@@ -51,7 +51,7 @@ class Stats(ctypes.Structure):
         ("cand_ids", ctypes.c_int64), ("proposals", ctypes.c_int64), ("bucket_overflow", ctypes.c_int64), ("reordered", ctypes.c_int32),
         ("join_launches", ctypes.c_int32), ("join_ms", ctypes.c_double), ("join_ran", ctypes.c_int32),
         ("join_path", ctypes.c_int32), ("join_ms_ran", ctypes.c_double), ("merge_ms_ran", ctypes.c_double),
-        ("sample_ms_ran", ctypes.c_double),
+        ("sample_ms_ran", ctypes.c_double), ("reorder_ms", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:

@@ -150,6 +150,7 @@ struct knng_ctx {
     std::vector<cudaEvent_t> ev;  // per timed iteration: before count, after sampling, before join,
                                   // after join, after merge
     std::vector<int> ev_li;       // iteration index of each pair
+    std::vector<cudaEvent_t> rev; // start/stop pairs around relabellings (KNNG_FLAG_TIMING)
 
     DevState dev(bool gate) const {
         DevState st;
@@ -404,6 +405,12 @@ int ctx_check(knng_ctx *c) {
 
 int enqueue_reorder(knng_ctx *c) {
     if (!c->sigma) return KNNG_ERR_STATE;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (c->flags & KNNG_FLAG_TIMING) {
+        for (auto &e : ev) KNNG_TRY(cudaEventCreate(&e));
+        for (auto &e : ev) c->rev.push_back(e);
+        KNNG_TRY(cudaEventRecord(ev[0], c->stream));
+    }
     if (c->rscratch) {
         int nl = 0;
         KNNG_TRY(launch_parallel_relabel(c->X, c->keys, c->n, c->K, c->nv, c->sigma, c->rscratch, &nl, c->stream));
@@ -416,6 +423,7 @@ int enqueue_reorder(knng_ctx *c) {
     DevState st = c->dev(false);
     KNNG_TRY(launch_permute(st, c->X2, c->keys2, c->sigma, c->total_perm, c->stream));
     c->launches++;
+    if (ev[1]) KNNG_TRY(cudaEventRecord(ev[1], c->stream));
     std::swap(c->X, c->X2);
     std::swap(c->keys, c->keys2);
     if (c->bf16) {
@@ -808,6 +816,12 @@ int knng_get_stats(knng_ctx *c, knng_stats *out) {
         }
     }
     out->bucket_overflow = st[kStatBucketOverflow];
+    out->reorder_ms = 0;
+    for (size_t i = 0; i + 1 < c->rev.size(); i += 2) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, c->rev[i], c->rev[i + 1]) == cudaSuccess) out->reorder_ms += ms;
+        else cudaGetLastError();
+    }
     return KNNG_OK;
 }
 
@@ -819,6 +833,7 @@ int knng_destroy(knng_ctx *c) {
     }
     if (c->capture) cudaStreamDestroy(c->capture);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->rev) cudaEventDestroy(e);
     if (c->arena) cudaFreeAsync(c->arena, c->stream);
     if (c->barena) cudaFreeAsync(c->barena, c->stream);
     delete c;
@@ -989,6 +1004,7 @@ void add_stats(knng_stats &a, const knng_stats &b) {
     a.join_ms_ran += b.join_ms_ran;
     a.merge_ms_ran += b.merge_ms_ran;
     a.sample_ms_ran += b.sample_ms_ran;
+    a.reorder_ms += b.reorder_ms;
 }
 
 }  // namespace
