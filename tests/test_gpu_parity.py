@@ -634,3 +634,72 @@ def test_parallel_relabel_builds_and_periodic_relabels():
     assert sorted(sg.tolist()) == list(range(len(x)))
     assert metrics.check_graph(x, gi, gd) == []
     assert metrics.recall(x, gi, ei, rows) >= rp - 0.01
+
+
+# ------------------------------------------------------------ edge cases ----
+
+@pytest.mark.parametrize("n,d,K,rows", [
+    (50, 3, 1, None),          # one query tile, one point tile, K = 1
+    (4096, 1, 5, None),        # d = 1 (one 16-wide bf16 k-block, 15 zero columns)
+    (5000, 125, 32, [7]),      # a single query row, rows padded to 128 columns
+    (6000, 16, 10, [3, 3, 5999, 0, 3]),  # repeated query rows
+])
+def test_tensor_core_bruteforce_edges(n, d, K, rows, monkeypatch):
+    x = workloads.gaussian_mixture(n, d, 7, seed=n + d)
+    r = None if rows is None else torch.tensor(rows, dtype=torch.int64, device="cuda")
+    monkeypatch.setenv("KNNG_TEST_BF_PATH", "tensor")
+    ti, td = knng.knng_bruteforce(_cuda(x), K, rows=r)
+    assert knng.bruteforce_last_fallbacks() >= 0
+    monkeypatch.setenv("KNNG_TEST_BF_PATH", "cuda")
+    ci, cd = knng.knng_bruteforce(_cuda(x), K, rows=r)
+    assert torch.equal(ti, ci) and torch.equal(td, cd)
+
+
+def test_tensor_core_bruteforce_identical_points(monkeypatch):
+    """All points equal: every distance is 0, the answer is the K smallest
+    ids other than the query, and no bound can separate the candidates (the
+    exact kernel redoes what the bound cannot certify)."""
+    x = np.ones((5000, 24), np.float32)
+    monkeypatch.setenv("KNNG_TEST_BF_PATH", "tensor")
+    ti, td = knng.knng_bruteforce(_cuda(x), 8)
+    monkeypatch.setenv("KNNG_TEST_BF_PATH", "cuda")
+    ci, cd = knng.knng_bruteforce(_cuda(x), 8)
+    assert torch.equal(ti, ci) and torch.equal(td, cd) and float(td.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("n,K,rho", [(3, 1, 1.0), (200, 1, 0.5), (500, 12, 0.05)])
+def test_heap_sampling_small_cases_match_oracle(n, K, rho):
+    x = _int_data(n, 3, 7, seed=n)
+    gi, gd, st = knng.knng_build(_cuda(x), K, rho=rho, delta=0.0, max_iters=5, seed=2,
+                                 flags=knng.FLAG_HEAP_SAMPLING)
+    oi, od, ost = oracle.build_knng(x, K, rho, 0.0, 5, seed=2, sampler="heap")
+    assert st["iterations"] == ost["iters"]
+    assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+def test_parallel_relabel_edges():
+    """n = 2; two disconnected halves (each list points into its own half);
+    all points equal (every distance ties, so ids decide)."""
+    flags = knng.FLAG_REORDER | knng.FLAG_REORDER_PARALLEL
+    cases = []
+    cases.append((np.array([[0.0], [1.0]], np.float32), np.array([[1], [0]], np.int32)))
+    n, K = 400, 4
+    g = np.random.default_rng(5)
+    ids = np.empty((n, K), np.int32)
+    for u in range(n):
+        lo = 0 if u < n // 2 else n // 2
+        ids[u] = lo + g.choice([v for v in range(n // 2) if lo + v != u], K, replace=False)
+    cases.append((_int_data(n, 2, 4, seed=1), ids))
+    ids2, _ = workloads.random_graph(300, 5, seed=9, p_new=1.0)
+    cases.append((np.zeros((300, 4), np.float32), ids2))
+    for x, ids in cases:
+        n, K = ids.shape
+        with knng.Context(_cuda(x), K, rho=1.0, flags=flags, graph=(ids, np.ones_like(ids, np.uint8))) as c:
+            c.reorder()
+            sg = c.permutation()
+        levels, _, _ = oracle.parallel_relabel(x, ids)
+        assert sorted(sg.tolist()) == list(range(n))
+        assert _contiguous(levels, sg)
+        if n == 400:
+            assert len(np.unique(levels[-1])) == 2
+            assert set(sg[: n // 2].tolist()) in (set(range(n // 2)), set(range(n // 2, n)))
