@@ -84,6 +84,21 @@ __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, int 
         "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(0), "r"(0), "r"(g), "r"(su32(bar))
         : "memory");
 }
+// 2-d tile load (coordinates x = column, y = row) into shared memory
+__device__ __forceinline__ void tma_load2(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+// shared-memory matrix descriptor, 128-byte swizzle, K-major: rows of 128 B,
+// 8-row groups 1,024 B apart (LBO unused); a k-step inside the 64-element
+// swizzle atom advances the start address by 32 B
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
 // shared-memory matrix descriptor: no swizzle, K-direction core stride lbo,
 // 8-row-group stride sbo
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -196,7 +211,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     bf_tc_kernel(const __grid_constant__ CUtensorMap mqh, const __grid_constant__ CUtensorMap mql,
                  const __grid_constant__ CUtensorMap mxh, const __grid_constant__ CUtensorMap mxl,
                  const float *__restrict__ qn, const float *__restrict__ xn, const int64_t *__restrict__ qrow,
-                 int64_t nq, int64_t n, int dpb, int64_t tiles_per_slice, uint64_t *__restrict__ part,
+                 int64_t nq, int64_t n, int dpb, int sw, int64_t tiles_per_slice, uint64_t *__restrict__ part,
                  int *__restrict__ err) {
     __shared__ TcShared sh;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -239,9 +254,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp == 0) {
         // ---- loader
         if (lane == 0) {
+            // an operand tile: one 4-d core-matrix box, or (128-byte swizzle)
+            // one 128-row x 64-column box per 16 KB block
+            auto load_tile = [&](unsigned char *dst, const CUtensorMap *m, int64_t row0, uint64_t *bar) {
+                if (sw) {
+                    for (int b = 0; b < dpb / 64; ++b) tma_load2(dst + b * 16384, m, b * 64, (int)row0, bar);
+                } else {
+                    tma_load(dst, m, (int)(row0 / 8), bar);
+                }
+            };
             bar_expect(&sh.a_full, 2 * tile_bytes);
-            tma_load(sqh, &mqh, (int)(q0 / 8), &sh.a_full);
-            tma_load(sql, &mql, (int)(q0 / 8), &sh.a_full);
+            load_tile(sqh, &mqh, q0, &sh.a_full);
+            load_tile(sql, &mql, q0, &sh.a_full);
             int64_t issued = 0;
             for (int64_t t = t0; t < t1; ++t) {
                 const int64_t it = t - t0;
@@ -251,8 +275,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     break;
                 }
                 bar_expect(&sh.b_full[s], 2 * tile_bytes);
-                tma_load(sxh(s), &mxh, (int)(t * kTcRows / 8), &sh.b_full[s]);
-                tma_load(sxl(s), &mxl, (int)(t * kTcRows / 8), &sh.b_full[s]);
+                load_tile(sxh(s), &mxh, t * kTcRows, &sh.b_full[s]);
+                load_tile(sxl(s), &mxl, t * kTcRows, &sh.b_full[s]);
                 ++issued;
             }
             // the copies this warp issued land before the block can exit
@@ -276,10 +300,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const uint32_t d = tmem + (uint32_t)a * 128;
                 const uint32_t qh = su32(sqh), ql = su32(sql), xh = su32(sxh(s)), xl = su32(sxl(s));
                 for (int k = 0; k < dpb / 16; ++k) {
-                    const uint32_t off = (uint32_t)k * 256;  // two K-direction core matrices
-                    mma(d, smem_desc(qh + off, lbo, sbo), smem_desc(xh + off, lbo, sbo), k > 0);
-                    mma(d, smem_desc(qh + off, lbo, sbo), smem_desc(xl + off, lbo, sbo), true);
-                    mma(d, smem_desc(ql + off, lbo, sbo), smem_desc(xh + off, lbo, sbo), true);
+                    if (sw) {
+                        // 64-column block k / 4, k-step k % 4 inside its swizzle atom
+                        const uint32_t off = (uint32_t)(k >> 2) * 16384 + (uint32_t)(k & 3) * 32;
+                        mma(d, smem_desc_sw128(qh + off), smem_desc_sw128(xh + off), k > 0);
+                        mma(d, smem_desc_sw128(qh + off), smem_desc_sw128(xl + off), true);
+                        mma(d, smem_desc_sw128(ql + off), smem_desc_sw128(xh + off), true);
+                    } else {
+                        const uint32_t off = (uint32_t)k * 256;  // two K-direction core matrices
+                        mma(d, smem_desc(qh + off, lbo, sbo), smem_desc(xh + off, lbo, sbo), k > 0);
+                        mma(d, smem_desc(qh + off, lbo, sbo), smem_desc(xl + off, lbo, sbo), true);
+                        mma(d, smem_desc(ql + off, lbo, sbo), smem_desc(xh + off, lbo, sbo), true);
+                    }
                 }
                 mma_commit(&sh.b_empty[s]);
                 mma_commit(&sh.t_full[a]);
@@ -523,9 +555,20 @@ EncodeTiledFn encode_fn() {
 // rows x dpb bf16 (rows a multiple of 128) as the 4-d tensor (kk 8, r 8, c dpb/8,
 // g rows/8) with byte strides (r: dpb*2, c: 16, g: 8*dpb*2): a box of
 // (8, 8, dpb/8, 16) lands as [g][c][r][kk], the canonical core-matrix order
-bool encode_map(CUtensorMap *m, const void *base, int64_t rows, int dpb) {
+bool encode_map(CUtensorMap *m, const void *base, int64_t rows, int dpb, bool sw) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
+    if (sw) {
+        // rows x dpb bf16 as a 2-d tensor; a 64 x 128 box lands as 128 rows of
+        // 128 B with the 128-byte swizzle (16-byte chunk c of row r at c ^ (r % 8))
+        const cuuint64_t dims2[2] = {(cuuint64_t)dpb, (cuuint64_t)rows};
+        const cuuint64_t strides2[1] = {(cuuint64_t)dpb * 2};
+        const cuuint32_t box2[2] = {64, kTcRows};
+        const cuuint32_t es2[2] = {1, 1};
+        return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims2, strides2, box2, es2,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     const cuuint64_t dims[4] = {8, 8, (cuuint64_t)dpb / 8, (cuuint64_t)rows / 8};
     const cuuint64_t strides[3] = {(cuuint64_t)dpb * 2, 16, (cuuint64_t)dpb * 16};
     const cuuint32_t box[4] = {8, 8, (cuuint32_t)dpb / 8, kTcRows / 8};
@@ -534,10 +577,15 @@ bool encode_map(CUtensorMap *m, const void *base, int64_t rows, int dpb) {
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+// operand width: rows of more than 32 floats take the 128-byte-swizzle layout
+// (whole 64-column blocks), narrower rows the core-matrix layout (16 columns)
+bool tc_swizzled(int dp) { return dp > 32; }
+int tc_dpb(int dp) { return tc_swizzled(dp) ? (dp + 63) & ~63 : (dp + 15) & ~15; }
 }  // namespace
 
 size_t bruteforce_tc_scratch(int64_t n, int64_t nq, int dp, int K, int *slices_out) {
-    const int dpb = (dp + 15) & ~15;
+    const int dpb = tc_dpb(dp);
     const int64_t npad = (n + kTcRows - 1) / kTcRows * kTcRows, qpad = (nq + kTcRows - 1) / kTcRows * kTcRows;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -565,7 +613,7 @@ size_t bruteforce_tc_scratch(int64_t n, int64_t nq, int dp, int K, int *slices_o
            al((size_t)nq * K * 8);
 }
 
-bool bruteforce_tc_supported(int dp) { return ((dp + 15) & ~15) <= 128 && encode_fn() != nullptr; }
+bool bruteforce_tc_supported(int dp) { return tc_dpb(dp) <= 128 && encode_fn() != nullptr; }
 
 namespace {
 // CUDA events around the prefilter launch, per thread, made on first use on
@@ -582,7 +630,8 @@ thread_local PrefilterEvents g_pf_events;
 cudaError_t launch_bruteforce_tc(const float *X, int64_t n, int dp, int d, int K, const int64_t *rows, int64_t nq,
                                  int32_t *ids, float *dists, cudaStream_t s, unsigned char *scratch, int S,
                                  int *nredo_host, float *prefilter_ms) {
-    const int dpb = (dp + 15) & ~15;
+    const int dpb = tc_dpb(dp);
+    const bool sw = tc_swizzled(dp);
     const int64_t npad = (n + kTcRows - 1) / kTcRows * kTcRows, qpad = (nq + kTcRows - 1) / kTcRows * kTcRows;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     unsigned char *p = scratch;
@@ -617,8 +666,8 @@ cudaError_t launch_bruteforce_tc(const float *X, int64_t n, int dp, int d, int K
     bf_split_kernel<<<gs, 256, 0, s>>>(X, dp, d, rows, mu, nq, qpad, dpb, qh, ql, qn, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     CUtensorMap mqh, mql, mxh, mxl;
-    if (!encode_map(&mqh, qh, qpad, dpb) || !encode_map(&mql, ql, qpad, dpb) || !encode_map(&mxh, xh, npad, dpb) ||
-        !encode_map(&mxl, xl, npad, dpb))
+    if (!encode_map(&mqh, qh, qpad, dpb, sw) || !encode_map(&mql, ql, qpad, dpb, sw) ||
+        !encode_map(&mxh, xh, npad, dpb, sw) || !encode_map(&mxl, xl, npad, dpb, sw))
         return cudaErrorNotSupported;
     const size_t dyn = 1024 + (size_t)(2 + 2 * kTcStages) * kTcRows * dpb * 2;
     static bool opted = false;
@@ -638,7 +687,7 @@ cudaError_t launch_bruteforce_tc(const float *X, int64_t n, int dp, int d, int K
     }
     if ((e = cudaEventRecord(ev.a, s)) != cudaSuccess) return e;
     bf_tc_kernel<<<dim3((unsigned)(qpad / kTcRows), (unsigned)S), kTcThreads, dyn, s>>>(
-        mqh, mql, mxh, mxl, qn, xn, rows, nq, n, dpb, per, part, counters + 1);
+        mqh, mql, mxh, mxl, qn, xn, rows, nq, n, dpb, sw ? 1 : 0, per, part, counters + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaEventRecord(ev.b, s)) != cudaSuccess) return e;
     const int gr = grid_for((const void *)bf_rerank_kernel, 256, 0);
