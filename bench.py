@@ -553,7 +553,7 @@ def run_gpu(args):
     # library on the launching stream, algorithmic bytes from device counters
     flush.fill_(1)
     torch.cuda.synchronize()
-    # (events inside a captured graph cannot be timed: this build runs ungraphed)
+    # (events inside a captured graph cannot be timed: this extra build runs without one)
     _, _, tst = knng.knng_build(xd, w.K, w.rho, w.delta, w.max_iters, seed=0,
                                 flags=(flags & ~knng.FLAG_GRAPH) | knng.FLAG_TIMING)
     torch.cuda.synchronize()

@@ -4,7 +4,7 @@ bench.py times (knng_build with each workload's parameters, seed 0).
 The oracle's NN-Descent cannot run at these sizes in a test, so the checks
 are the properties that hold at any size, on sampled rows:
 - list invariants and every returned distance within 1e-4 of its float64
-  recomputation (the north_star audit);
+  recomputation (the accuracy audit);
 - the GPU brute force equals the oracle's brute force on sampled rows (ids up
   to ties), so it can serve as ground truth for recall on more rows;
 - recall at the level measured for the workload, and bf16 within 0.01 of
