@@ -4,23 +4,28 @@
 // any query the bound cannot certify.
 //
 // Prefilter (bf_tc_kernel, one CTA per 128 queries and one slice of the
-// points): every point x and query q is split into two bf16 terms (x = xh +
-// xl + r, |r| <= 2^-16 |x| per element) and q.x is taken as qh.xh + qh.xl +
-// ql.xh on the tensor cores (tcgen05.mma, M=128 queries x N=128 points, K=16,
-// float32 accumulate in tensor memory).  Operand tiles arrive by TMA
-// (cp.async.bulk.tensor) in the canonical no-swizzle K-major core-matrix
-// layout: 8 rows x 16 bytes per core matrix, K-direction core stride 128 B,
-// 8-row-group stride dpb * 16 B.  Warp 0 issues the loads, warp 1 the MMAs
-// into two alternating TMEM accumulators, warps 4..11 (two per TMEM
-// subpartition, 64 columns each) turn a finished tile into approximate
-// distances D' = |q|^2 + |x|^2 - 2 q.x and keep the 32 smallest per query
-// in registers.
-// Re-rank (bf_rerank_kernel, one warp per query): every kept candidate gets
-// its canonical float32 difference-form distance; the K smallest by
-// (dist, id) are the answer if every point outside the kept sets provably has
-// a larger distance: D'(y) >= tau (the smallest "worst kept" value of the
-// lists), and |D' - D| <= E(q), so D(y) >= tau - E(q) must exceed the K-th
-// kept distance.  Otherwise the query is listed for the exact kernel.
+// points): the points are centred on a sampled mean (distances do not change,
+// the error bound shrinks) and every point x and query q is split into two
+// bf16 terms (x = xh + xl + r, |r| <= 2^-16 |x| per element); q.x is taken as
+// qh.xh + qh.xl + ql.xh on the tensor cores (tcgen05.mma, M=128 queries x
+// N=128 points, K=16, float32 accumulate in tensor memory).  Operand tiles
+// arrive by TMA (cp.async.bulk.tensor): rows of more than 32 floats as 2-d
+// boxes of whole 128-byte rows with the 128-byte swizzle (SWIZZLE_128B
+// descriptors, 1 KB between 8-row groups, +32 B per k-step inside a 64-column
+// block); narrower rows in the no-swizzle K-major core-matrix layout (8 rows
+// x 16 bytes per core matrix, K-direction stride 128 B, 8-row-group stride
+// dpb * 16 B).  Warp 0 issues the loads, warp 1 the MMAs into two
+// alternating TMEM accumulators, warps 4..11 (two per TMEM subpartition, 64
+// columns each) turn a finished tile into approximate distances
+// D' = |q|^2 + |x|^2 - 2 q.x and keep the 32 smallest per query in registers,
+// testing a whole tile at once through the minimum of its 64 values.
+// Re-rank (bf_rerank_kernel, one warp per query): the kept lists are merged
+// to their 64 smallest D', which get the canonical float32 difference-form
+// distance; the K smallest by (dist, id) are the answer if every point
+// outside those 64 provably has a larger distance: D'(y) >= T (the smallest
+// "worst kept" value of the full lists, or the 64th merged one), and
+// |D' - D| <= E(q), so D(y) >= T - E(q) must exceed the K-th distance.
+// Otherwise the query is listed for the exact kernel.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
