@@ -263,6 +263,18 @@ int knng_bruteforce_last_fallbacks(void);
 float knng_bruteforce_last_prefilter_ms(void);
 
 /*
+ * Measurement helper (not in the paper): the rate at which this GPU reads a
+ * buffer that stays in its L2, the denominator of the roofline of kernels
+ * whose working set fits there.  Allocates `bytes` (at least 1 MiB; choose
+ * well below the L2 size) on the current device, reads it once, then times one
+ * launch that reads it `passes` times with 16-byte loads cached in L2 only.
+ * *gbs = bytes * passes / time, in GB/s.  Synchronises `stream` (NULL = the
+ * legacy default stream).  Errors: KNNG_ERR_INVALID_ARG, KNNG_ERR_OOM,
+ * KNNG_ERR_CUDA.
+ */
+int knng_measure_l2_read(int64_t bytes, int passes, void *stream, double *gbs);
+
+/*
  * Brute-force K-NNG that allocates nothing, for callers that cannot allocate
  * device memory: code that runs while a stream is being captured into a CUDA
  * graph in global capture mode (where cudaMalloc is refused), programs whose

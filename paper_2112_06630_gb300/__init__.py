@@ -18,7 +18,7 @@ from . import build as _build
 
 __all__ = [
     "KnngError", "Stats", "Context", "knng_build", "knng_build_batched", "knng_bruteforce", "lib_path", "Desc",
-    "bruteforce_last_fallbacks", "bruteforce_last_prefilter_ms",
+    "bruteforce_last_fallbacks", "bruteforce_last_prefilter_ms", "measure_l2_read",
     "FLAG_REORDER", "FLAG_REORDER_B", "FLAG_TIMING", "FLAG_GRAPH", "FLAG_BF16", "FLAG_AUTOTUNE", "FLAG_HEAP_SAMPLING", "FLAG_REORDER_PARALLEL", "version", "strerror", "load",
 ]
 
@@ -93,6 +93,7 @@ def _load():
         "knng_bruteforce": (i32, [P, i64, i32, i32, P, i64, P, P, P]),
         "knng_bruteforce_last_fallbacks": (i32, []),
         "knng_bruteforce_last_prefilter_ms": (f32, []),
+        "knng_measure_l2_read": (i32, [i64, i32, P, ctypes.POINTER(ctypes.c_double)]),
         "knng_build_batched": (i32, [P, i32, i32, f32, f32, i32, u64, u32, P, P]),
         "knng_strerror": (ctypes.c_char_p, [i32]),
         "knng_version": (ctypes.c_char_p, []),
@@ -258,6 +259,15 @@ def bruteforce_last_prefilter_ms() -> float:
     """CUDA-event time of this thread's last tensor-core prefilter kernel in
     milliseconds; -1 if the last knng_bruteforce did not take that path."""
     return float(_lib.knng_bruteforce_last_prefilter_ms())
+
+
+def measure_l2_read(nbytes: int = 32 << 20, passes: int = 200, stream=None) -> float:
+    """GB/s at which the GPU reads an L2-resident buffer (one launch, 16-byte
+    loads cached in L2 only)."""
+    out = ctypes.c_double(0.0)
+    _check(_lib.knng_measure_l2_read(nbytes, passes, _stream_ptr(stream, True), ctypes.byref(out)),
+           "knng_measure_l2_read")
+    return float(out.value)
 
 
 class Context:

@@ -1045,6 +1045,32 @@ int knng_bruteforce_last_fallbacks(void) { return g_bf_fallbacks; }
 
 float knng_bruteforce_last_prefilter_ms(void) { return g_bf_prefilter_ms; }
 
+int knng_measure_l2_read(int64_t bytes, int passes, void *stream, double *gbs) {
+    if (bytes < (1 << 20) || passes < 1 || !gbs) return KNNG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n4 = (size_t)bytes / 16;
+    unsigned char *buf = nullptr;
+    KNNG_TRY(lib_malloc((void **)&buf, n4 * 16 + 256, s));
+    float *sink = reinterpret_cast<float *>(buf + n4 * 16);
+    cudaEvent_t a = nullptr, b = nullptr;
+    float ms = 0.f;
+    cudaError_t e = cudaMemsetAsync(buf, 0, n4 * 16 + 256, s);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = launch_l2_read(buf, n4, 1, sink, s);  // brings the buffer into L2
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    if (e == cudaSuccess) e = launch_l2_read(buf, n4, passes, sink, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) return cuda_code(e);
+    *gbs = (double)n4 * 16.0 * passes / (ms / 1e3) / 1e9;
+    return KNNG_OK;
+}
+
 int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *rows, int64_t nq, int32_t *ids,
                     float *dists, void *stream) {
     if (!data || !ids || !dists || n < 2 || d < 1 || K < 1 || K > n - 1) return KNNG_ERR_INVALID_ARG;

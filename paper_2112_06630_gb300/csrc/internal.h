@@ -22,6 +22,8 @@ cudaError_t launch_count(const DevState &st, int li, cudaStream_t s);
 size_t parallel_relabel_scratch(int64_t n, int K);
 cudaError_t launch_parallel_relabel(const float *X, const uint64_t *keys, int64_t n, int K, int nv, int32_t *sigma,
                                     unsigned char *scratch, int *launches, cudaStream_t s);
+// l2probe.cu: `passes` reads of an n4 x 16-byte buffer in one launch
+cudaError_t launch_l2_read(const void *buf, size_t n4, int passes, float *sink, cudaStream_t s);
 cudaError_t launch_heap_sample(const DevState &st, int li, int it, uint64_t seed, cudaStream_t s);
 cudaError_t launch_sample(const DevState &st, int li, int it, uint64_t seed, cudaStream_t s);
 cudaError_t launch_join(const DevState &st, int li, cudaStream_t s);

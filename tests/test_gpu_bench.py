@@ -34,3 +34,18 @@ def test_bruteforce_bench_line(rows):
     assert 0 < roof["share_of_call"] <= 1
     assert line["e2e"]["h2d_bytes_per_step"] >= 20000 * 128 * 4
     assert line["gpu_launches"] >= 7 * 2
+
+
+def test_l2_read_rate_is_measured():
+    """The L2 read rate the roofline of L2-resident kernels is reported
+    against: positive, and a small buffer read many times is served from L2,
+    above the HBM copy rate."""
+    import json as _json
+    import paper_2112_06630_gb300 as knng
+    g = knng.measure_l2_read(32 << 20, 100)
+    assert g > 0
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks):
+        assert g > _json.load(open(peaks))["hbm_gbs"]
+    with pytest.raises(knng.KnngError):
+        knng.measure_l2_read(1024, 10)
