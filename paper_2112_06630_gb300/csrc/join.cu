@@ -44,6 +44,24 @@ __device__ __forceinline__ void cp_async8_w(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
 }
+// position of the r-th (from 0) set bit of x; r < popcount(x)
+__device__ __forceinline__ int nth_set_bit64(unsigned long long x, int r) {
+    const unsigned lo = (unsigned)x;
+    const int pl = __popc(lo);
+    unsigned w = r < pl ? lo : (unsigned)(x >> 32);
+    int rr = r < pl ? r : r - pl, pos = r < pl ? 0 : 32;
+#pragma unroll
+    for (int sh = 16; sh >= 1; sh >>= 1) {
+        const int c = __popc(w & ((1u << sh) - 1u));
+        if (rr >= c) {
+            rr -= c;
+            w >>= sh;
+            pos += sh;
+        }
+    }
+    return pos;
+}
+
 constexpr int kJoinWarps = 4;
 constexpr int kMergeWarps = 8;
 constexpr int kWarpMaxNv = 8;   // float32 rows of up to 32 floats take the warp kernel (measured crossover)
@@ -159,50 +177,86 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
                 atomicOr(&mw[2 * j + (i >> 5)], 1u << (i & 31));
         }
         __syncwarp();
-        // ---- 4. bucket runs: lane = target; one reservation per target, then
-        //         the lane writes its run (each key recomputed with the
-        //         arithmetic of step 3, so it is bit-identical); a proposal
-        //         whose run has no slot (bucket or pool spent) is marked for
-        //         the locked insertion
+        // ---- 4. bucket runs, flattened over the warp: lane t reserves
+        //         target t's range (one atomicAdd per target) and the pool
+        //         chunks of the runs it spans (one claim per run); then lane k
+        //         writes proposal k of the node -- its target found by a
+        //         binary search over the targets' prefix counts, its partner
+        //         as the r-th set bit of the target's mask -- so every lane
+        //         has work however unevenly the proposals fall.  Each key is
+        //         recomputed with the arithmetic of step 3 (bit-identical); a
+        //         proposal whose run has no slot (bucket or pool spent) is
+        //         marked for the locked insertion
         unsigned long long *fails = reinterpret_cast<unsigned long long *>(swk);  // swk is done
+        int *rbase = sid + kSetMax;  // per target: reserved start minus its prefix count
+        int inc0, inc1;              // inclusive prefix counts of targets lane and 32 + lane
+        {
+            const unsigned long long ma = (int)lane < ns ? mask[lane] : 0ull;
+            const unsigned long long mb = (int)lane + 32 < ns ? mask[lane + 32] : 0ull;
+            const int ca = __popcll(ma), cb = __popcll(mb);
+            int ba = 0, bb = 0;
+            if (ca) ba = atomicAdd(st.pcursor + sid[lane], ca);
+            if (cb) bb = atomicAdd(st.pcursor + sid[lane + 32], cb);
+            if (ca)
+                for (int r = ba >> kBucketRunBits > 1 ? ba >> kBucketRunBits : 1; r <= (ba + ca - 1) >> kBucketRunBits;
+                     ++r)
+                    bucket_slot(st, (uint32_t)sid[lane], r << kBucketRunBits);
+            if (cb)
+                for (int r = bb >> kBucketRunBits > 1 ? bb >> kBucketRunBits : 1; r <= (bb + cb - 1) >> kBucketRunBits;
+                     ++r)
+                    bucket_slot(st, (uint32_t)sid[lane + 32], r << kBucketRunBits);
+            l_props += ca + cb;
+            inc0 = ca;
+            inc1 = cb;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(kFull, inc0, o);
+                if ((int)lane >= o) inc0 += v;
+            }
+            const int tot0 = __shfl_sync(kFull, inc0, 31);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(kFull, inc1, o);
+                if ((int)lane >= o) inc1 += v;
+            }
+            inc1 += tot0;
+            if ((int)lane < ns) {
+                rbase[lane] = ba - (inc0 - ca);
+                fails[lane] = 0ull;
+            }
+            if ((int)lane + 32 < ns) {
+                rbase[lane + 32] = bb - (inc1 - cb);
+                fails[lane + 32] = 0ull;
+            }
+        }
+        const int total = __shfl_sync(kFull, inc1, 31);
+        __threadfence_block();
+        __syncwarp();
         unsigned ovf_lo = 0, ovf_hi = 0;  // targets with marked proposals
-        for (int t = lane; t < ns; t += 32) {
-            const unsigned long long mt = mask[t];
-            const int c = __popcll(mt);
-            if (!c) continue;
-            l_props += c;
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            const int k = k0 + (int)lane;
+            const bool act = k < total;
+            const int kk = act ? k : total - 1;
+            // target of proposal kk: the number of targets whose inclusive
+            // prefix count is <= kk (prefixes of targets past ns equal total)
+            int t = 0;
+#pragma unroll
+            for (int step = 32; step > 0; step >>= 1) {
+                const int probe = t + step - 1;
+                const int v0 = __shfl_sync(kFull, inc0, probe & 31), v1 = __shfl_sync(kFull, inc1, probe & 31);
+                if ((probe < 32 ? v0 : v1) <= kk) t += step;
+            }
+            const int tp = t > 0 ? t - 1 : 0;
+            const int e0 = __shfl_sync(kFull, inc0, tp & 31), e1 = __shfl_sync(kFull, inc1, tp & 31);
+            const int excl = t == 0 ? 0 : (tp < 32 ? e0 : e1);
+            if (!act) continue;
             const uint32_t p = (uint32_t)sid[t];
-            const int b = atomicAdd(st.pcursor + p, c);
-            const float4 *rt = kRowsSmem ? rows + t * rs : X4 + (size_t)p * nv;
-            unsigned long long mm = mt;
-            int fit = 0;
-            uint64_t *slot = nullptr;
-            for (; fit < c; ++fit, mm &= mm - 1) {
-                const int pos = b + fit;
-                if (fit == 0 || (pos & (kBucketRun - 1)) == 0) slot = bucket_slot(st, p, pos);
-                else ++slot;
-                if (!slot) break;
-                const int j = __ffsll((long long)mm) - 1;
+            const int j = nth_set_bit64(mask[t], k - excl);
+            uint64_t *slot = bucket_slot(st, p, k + rbase[t]);
+            if (slot) {
+                const float4 *rt = kRowsSmem ? rows + t * rs : X4 + (size_t)p * nv;
                 const float4 *rj = kRowsSmem ? rows + j * rs : X4 + (size_t)sid[j] * nv;
                 *slot = make_key(l2sq_rows(rt, rj, nv), (uint32_t)sid[j], kFlagNew | kFlagIns);
-            }
-            if (fit < c) {
-                // rare: a run without a slot; later runs of this range may
-                // still have one (claimed by another warp), and every slot of
-                // a valid run must be written -- mark only the proposals whose
-                // run has none
-                unsigned long long failed = 0ull;
-                for (; fit < c; ++fit, mm &= mm - 1) {
-                    const int j = __ffsll((long long)mm) - 1;
-                    uint64_t *d = bucket_slot(st, p, b + fit);
-                    if (d) {
-                        const float4 *rj = kRowsSmem ? rows + j * rs : X4 + (size_t)sid[j] * nv;
-                        *d = make_key(l2sq_rows(rt, rj, nv), (uint32_t)sid[j], kFlagNew | kFlagIns);
-                    } else {
-                        failed |= 1ull << j;
-                    }
-                }
-                fails[t] = failed;
+            } else {
+                atomicOr(&fails[t], 1ull << j);
                 if (t < 32) ovf_lo |= 1u << t;
                 else ovf_hi |= 1u << (t - 32);
             }
