@@ -44,24 +44,6 @@ __device__ __forceinline__ void cp_async8_w(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
 }
-// position of the r-th (from 0) set bit of x; r < popcount(x)
-__device__ __forceinline__ int nth_set_bit64(unsigned long long x, int r) {
-    const unsigned lo = (unsigned)x;
-    const int pl = __popc(lo);
-    unsigned w = r < pl ? lo : (unsigned)(x >> 32);
-    int rr = r < pl ? r : r - pl, pos = r < pl ? 0 : 32;
-#pragma unroll
-    for (int sh = 16; sh >= 1; sh >>= 1) {
-        const int c = __popc(w & ((1u << sh) - 1u));
-        if (rr >= c) {
-            rr -= c;
-            w >>= sh;
-            pos += sh;
-        }
-    }
-    return pos;
-}
-
 constexpr int kJoinWarps = 4;
 constexpr int kMergeWarps = 8;
 constexpr int kWarpMaxNv = 8;   // float32 rows of up to 32 floats take the warp kernel (measured crossover)

@@ -8,6 +8,24 @@
 namespace knng {
 
 constexpr int kSetMax = 64;      // candidates per node and iteration after repeats are removed
+
+// position of the r-th (from 0) set bit of x; r < popcount(x)
+__device__ __forceinline__ int nth_set_bit64(unsigned long long x, int r) {
+    const unsigned lo = (unsigned)x;
+    const int pl = __popc(lo);
+    unsigned w = r < pl ? lo : (unsigned)(x >> 32);
+    int rr = r < pl ? r : r - pl, pos = r < pl ? 0 : 32;
+#pragma unroll
+    for (int sh = 16; sh >= 1; sh >>= 1) {
+        const int c = __popc(w & ((1u << sh) - 1u));
+        if (rr >= c) {
+            rr -= c;
+            w >>= sh;
+            pos += sh;
+        }
+    }
+    return pos;
+}
 constexpr int kHashBits = 8;     // 256-slot hash set for repeat removal (at most 2 * (32 + 72) ids)
 constexpr int kLockSpins = 1 << 20;
 constexpr unsigned kFull = 0xFFFFFFFFu;
