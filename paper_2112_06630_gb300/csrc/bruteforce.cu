@@ -136,7 +136,7 @@ cudaError_t launch_bf_t(const float *X, int64_t n, int nv, int K, const int64_t 
     if (tile < 1) tile = 1;
     const size_t dyn = (size_t)tile * nv * 16;
     auto kern = bruteforce_kernel<KMAX, NVR>;
-    cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    cudaError_t e = smem_opt_in((const void *)kern, dyn);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (nq + kBfThreads - 1) / kBfThreads;
     const int64_t chunk = (n + S - 1) / S;

@@ -32,6 +32,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -543,9 +544,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn encode_fn() {
     static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static std::once_flag once;
+    std::call_once(once, [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
@@ -554,7 +554,7 @@ EncodeTiledFn encode_fn() {
             fn = reinterpret_cast<EncodeTiledFn>(p);
         else
             cudaGetLastError();
-    }
+    });
     return fn;
 }
 // rows x dpb bf16 (rows a multiple of 128) as the 4-d tensor (kk 8, r 8, c dpb/8,
@@ -675,13 +675,7 @@ cudaError_t launch_bruteforce_tc(const float *X, int64_t n, int dp, int d, int K
         !encode_map(&mxh, xh, npad, dpb, sw) || !encode_map(&mxl, xl, npad, dpb, sw))
         return cudaErrorNotSupported;
     const size_t dyn = 1024 + (size_t)(2 + 2 * kTcStages) * kTcRows * dpb * 2;
-    static bool opted = false;
-    if (!opted) {
-        e = cudaFuncSetAttribute((const void *)bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(1024 + (size_t)(2 + 2 * kTcStages) * kTcRows * 128 * 2));
-        if (e != cudaSuccess) return e;
-        opted = true;
-    }
+    if ((e = smem_opt_in((const void *)bf_tc_kernel, dyn)) != cudaSuccess) return e;
     const int64_t ntiles = npad / kTcRows, per = (ntiles + S - 1) / S;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;

@@ -11,6 +11,9 @@ namespace knng {
 
 // persistent grid size for a warp-per-item kernel: a multiple of the SM count
 int grid_for(const void *kernel, int block_threads, size_t dyn_smem);
+// opt `kernel` in to `bytes` of dynamic shared memory on the current device
+// (once per kernel, device and size; thread-safe)
+cudaError_t smem_opt_in(const void *kernel, size_t bytes);
 
 cudaError_t launch_stage(const float *src, int64_t n, int d, float *X, int dp, cudaStream_t s);
 cudaError_t launch_init_random(const DevState &st, uint64_t seed, int *err, cudaStream_t s);

@@ -521,16 +521,8 @@ cudaError_t launch_join_t(const DevState &st, int li, cudaStream_t s) {
     const JoinLayout lay = join_layout(st.cap, st.nv, S);
     const size_t dyn = lay.per_warp * kJoinWarps;
     auto kern = join_kernel<S>;
-    static bool opted_in = false;  // allow up to the per-block maximum once
-    if (!opted_in) {
-        int dev = 0, mx = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             mx - 1024);
-        if (e != cudaSuccess) return e;
-        opted_in = true;
-    }
+    cudaError_t e = smem_opt_in((const void *)kern, dyn);
+    if (e != cudaSuccess) return e;
     const int grid = grid_for((const void *)kern, kJoinWarps * 32, dyn);
     kern<<<grid, kJoinWarps * 32, dyn, s>>>(st, li);
     return cudaGetLastError();

@@ -3,6 +3,10 @@
 // greedy relabelling (Algorithm 1) with its permutation, and the re-ranked
 // output.  One warp owns one node's list wherever a list is touched, so list
 // rows (K <= 32 keys) map onto lanes.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "internal.h"
 
 namespace knng {
@@ -24,6 +28,24 @@ int grid_for(const void *kernel, int block_threads, size_t dyn_smem) {
         per_sm < 1)
         per_sm = 1;
     return sms * per_sm;
+}
+
+// Dynamic shared memory above the 48 KB default needs a per-function opt-in,
+// and the attribute belongs to the current device's context: record the
+// largest size granted per (kernel, device) under a lock.
+cudaError_t smem_opt_in(const void *kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> granted;
+    std::lock_guard<std::mutex> g(mu);
+    size_t &have = granted[{kernel, dev}];
+    if (have >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
 }
 
 // ------------------------------------------------------------------ stage ----

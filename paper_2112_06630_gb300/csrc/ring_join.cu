@@ -774,12 +774,8 @@ template <bool kBF16>
 cudaError_t launch_ring_t(const DevState &st, int li, cudaStream_t s) {
     auto kern = ring_join_kernel<kBF16>;
     constexpr uint32_t dyn = kRingBytes;
-    static bool opted_in = false;
-    if (!opted_in) {
-        cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-        opted_in = true;
-    }
+    cudaError_t e = smem_opt_in((const void *)kern, dyn);
+    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -400,13 +400,8 @@ cudaError_t launch_tile_t(const DevState &st, int li, cudaStream_t s) {
     size_t dyn = kBF16 ? 2ull * kSetMax * kStrideB * sizeof(uint16_t) : 2ull * kSetMax * kStrideV * 16;
     dyn = std::max(dyn, (size_t)kSetMax * (kMaxK + 1) * sizeof(uint64_t));
     auto kern = tile_join_kernel<kBF16>;
-    static bool opted_in = false;
-    if (!opted_in) {
-        cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)dyn);
-        if (e != cudaSuccess) return e;
-        opted_in = true;
-    }
+    cudaError_t e = smem_opt_in((const void *)kern, dyn);
+    if (e != cudaSuccess) return e;
     const int grid = grid_for((const void *)kern, kTileThreads, dyn);
     kern<<<grid, kTileThreads, dyn, s>>>(st, li);
     return cudaGetLastError();
