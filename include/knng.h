@@ -68,7 +68,8 @@ extern "C" {
                                         priority hi32(h(seed, 4, it, u, j)) for both of its offers (v to
                                         u, u to v, of the edge's new/old kind); each node keeps per kind
                                         the s smallest (priority, id) offers, one per id; forward new
-                                        entries kept as new candidates lose their flag */
+                                        entries kept as new candidates lose their flag; requires
+                                        n * K < 2^31 (else KNNG_ERR_UNSUPPORTED) */
 #define KNNG_FLAG_REORDER_PARALLEL 0x80u /* with REORDER: relabel by the data-parallel variant instead of
                                            Algorithm 1 -- single-linkage (Boruvka) rounds on the list graph,
                                            edges ordered by (float32 distance, min id, max id), every

@@ -355,6 +355,11 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
     // bf16 tensor-core dots where the contraction is long enough to pay
     c->bf16 = (flags & KNNG_FLAG_BF16) && d >= 64;
     c->heap = (flags & KNNG_FLAG_HEAP_SAMPLING) != 0;
+    // the reverse-offer segments are addressed with 32-bit offsets
+    if (c->heap && (int64_t)n * K >= ((int64_t)1 << 31)) {
+        delete c;
+        return KNNG_ERR_UNSUPPORTED;
+    }
     c->dpb = (d + 63) & ~63;
     // test hook: run another join kernel the context can use (parity of the
     // three kernels on the same inputs)
