@@ -628,7 +628,7 @@ def run_gpu(args):
     # it, timed the same way (same rows, same flush, same step count)
     at99 = None
     if rec < 0.99 and not args.rho:
-        for r in (0.6, 0.7, 0.8, 1.0):
+        for r in (0.55, 0.6, 0.7, 0.8, 1.0):
             if r <= w.rho:
                 continue
             for _ in range(args.warmup):
