@@ -79,3 +79,24 @@ def test_null_pointers_rejected(lib):
     assert lib.knng_init(ctypes.byref(h), None, 10, 4, 3, 0.5, 0.0, 0, 0, None) == -1
     assert lib.knng_iterate(None, None) == -1
     assert lib.knng_destroy(None) == 0
+
+
+def test_header_compiles_as_c11(tmp_path):
+    """The header is usable from plain C: a C11 translation unit that takes
+    the address of every declared call compiles without warnings."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not available")
+    names = declared_functions()
+    src = tmp_path / "use_knng.c"
+    src.write_text('#include "knng.h"\n#include <stddef.h>\n'
+                   "const void *knng_calls[] = {\n"
+                   + "".join(f"    (const void *)&{n},\n" for n in names)
+                   + "    NULL\n};\n")
+    cuda_inc = "/usr/local/cuda/include"
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-c", str(src), "-o",
+                        str(tmp_path / "use_knng.o"), f"-I{os.path.join(ROOT, 'include')}", f"-I{cuda_inc}"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
