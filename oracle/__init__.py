@@ -35,44 +35,52 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+P_ = ctypes.c_void_p
+_i64, _i32, _u64, _f32t = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_float
+# name -> (result type, argument types) of every exported oracle function
+_SIGS = {
+    "orc_hash": (_u64, [_u64, ctypes.c_uint32, ctypes.c_uint32, _u64, _u64]),
+    "orc_dist64": (ctypes.c_double, [P_, P_, _i32]),
+    "orc_bruteforce": (_i32, [P_, _i64, _i32, _i32, P_, P_]),
+    "orc_bruteforce_rows": (_i32, [P_, _i64, _i32, _i32, P_, _i64, P_, P_]),
+    "orc_create": (P_, [P_, _i64, _i32, _i32, _f32t, _u64]),
+    "orc_init_random": (_i32, [P_]),
+    "orc_init_graph": (_i32, [P_, P_, P_, _i32]),
+    "orc_sample": (_i32, [P_, _i32, P_]),
+    "orc_sample_heap": (_i32, [P_, _i32, P_]),
+    "orc_set_sampler": (_i32, [P_, _i32]),
+    "orc_join": (_i32, [P_, P_]),
+    "orc_iterate": (_i32, [P_, P_]),
+    "orc_reorder": (_i32, [P_, _i32]),
+    "orc_get_samples": (_i32, [P_, _i32, P_, P_, P_, P_]),
+    "orc_set_samples": (_i32, [P_, _i32, P_, P_, P_, P_]),
+    "orc_get_state": (_i32, [P_, P_, P_, P_]),
+    "orc_get_graph": (_i32, [P_, P_, P_]),
+    "orc_get_sigma": (_i32, [P_, P_]),
+    "orc_free": (None, [P_]),
+    "orc_greedy_reorder": (_i32, [P_, _i64, _i32, _i32, P_, P_]),
+    "orc_parallel_relabel": (_i32, [P_, _i64, _i32, _i32, P_, _i32, P_, P_, P_, P_]),
+    "orc_build": (_i32, [P_, _i64, _i32, _i32, _f32t, _f32t, _i32, _u64, _i32, _i32, _i32, P_, P_, P_]),
+}
+
+
+def _bind(lib):
+    """Set the result and argument types of every oracle function on a loaded
+    library (the built oracle, or a deliberately mutated copy in a test)."""
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
-        P = ctypes.c_void_p
-        i64, i32, u64, f32 = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_float
-        sig = {
-            "orc_hash": (u64, [u64, ctypes.c_uint32, ctypes.c_uint32, u64, u64]),
-            "orc_dist64": (ctypes.c_double, [P, P, i32]),
-            "orc_bruteforce": (i32, [P, i64, i32, i32, P, P]),
-            "orc_bruteforce_rows": (i32, [P, i64, i32, i32, P, i64, P, P]),
-            "orc_create": (P, [P, i64, i32, i32, f32, u64]),
-            "orc_init_random": (i32, [P]),
-            "orc_init_graph": (i32, [P, P, P, i32]),
-            "orc_sample": (i32, [P, i32, P]),
-            "orc_sample_heap": (i32, [P, i32, P]),
-            "orc_set_sampler": (i32, [P, i32]),
-            "orc_join": (i32, [P, P]),
-            "orc_iterate": (i32, [P, P]),
-            "orc_reorder": (i32, [P, i32]),
-            "orc_get_samples": (i32, [P, i32, P, P, P, P]),
-            "orc_set_samples": (i32, [P, i32, P, P, P, P]),
-            "orc_get_state": (i32, [P, P, P, P]),
-            "orc_get_graph": (i32, [P, P, P]),
-            "orc_get_sigma": (i32, [P, P]),
-            "orc_free": (None, [P]),
-            "orc_greedy_reorder": (i32, [P, i64, i32, i32, P, P]),
-            "orc_parallel_relabel": (i32, [P, i64, i32, i32, P, i32, P, P, P, P]),
-            "orc_build": (i32, [P, i64, i32, i32, f32, f32, i32, u64, i32, i32, i32, P, P, P]),
-        }
-        for name, (res, args) in sig.items():
-            fn = getattr(lib, name)
-            fn.restype = res
-            fn.argtypes = args
-        _lib = lib
-        return lib
+        _lib = _bind(ctypes.CDLL(build()))
+        return _lib
 
 
 def _p(a: np.ndarray):

@@ -40,11 +40,15 @@ def recall(data, approx_ids, exact_ids, rows=None, rtol: float = 1e-6) -> float:
     dk = sqdist64(data, rows, exact_ids).max(axis=1)
     da = sqdist64(data, rows, a)
     hits = (da <= dk[:, None] * (1.0 + rtol) + 1e-30)
-    # a repeated id counts once
-    srt = np.sort(a, axis=1)
-    dup = np.zeros_like(hits)
-    dup[:, 1:] = srt[:, 1:] == srt[:, :-1]
-    return float(hits.sum() - dup.sum()) / float(len(rows) * K)
+    # recall is a set measure: a repeated id is one neighbour, so every copy of
+    # an id after its first is dropped, whether that id is a hit or a miss
+    order = np.argsort(a, axis=1, kind="stable")
+    srt = np.take_along_axis(a, order, axis=1)
+    dup_sorted = np.zeros(a.shape, dtype=bool)
+    dup_sorted[:, 1:] = srt[:, 1:] == srt[:, :-1]
+    dup = np.empty_like(dup_sorted)
+    np.put_along_axis(dup, order, dup_sorted, axis=1)
+    return float((hits & ~dup).sum()) / float(len(rows) * K)
 
 
 def check_graph(data, ids, dists, rtol: float = 1e-4, atol: float = 1e-6, rows=None):
