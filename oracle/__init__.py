@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle library in place (gcc); returns its path."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
+        subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm", "-lpthread"], check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -61,6 +61,9 @@ _SIGS = {
     "orc_greedy_reorder": (_i32, [P_, _i64, _i32, _i32, P_, P_]),
     "orc_parallel_relabel": (_i32, [P_, _i64, _i32, _i32, P_, _i32, P_, P_, P_, P_]),
     "orc_build": (_i32, [P_, _i64, _i32, _i32, _f32t, _f32t, _i32, _u64, _i32, _i32, _i32, P_, P_, P_]),
+    "orc_build_mt": (_i32, [P_, _i64, _i32, _i32, _f32t, _f32t, _i32, _u64, _i32, P_, P_, P_]),
+    "orc_default_threads": (_i32, []),
+    "orc_set_mt_block_pairs": (_i32, [_i64]),
 }
 
 
@@ -176,6 +179,27 @@ def build_knng(data, K: int, rho: float, delta: float, max_iters: int, seed: int
         raise ValueError(f"orc_build failed ({rc})")
     return ids, dists, dict(iters=int(st[0]), evals=int(st[1]), last_changes=int(st[2]),
                             reordered=bool(st[3]))
+
+
+def build_knng_mt(data, K: int, rho: float, delta: float, max_iters: int, seed: int = 0, threads: int = 0):
+    """Whole NN-Descent in batched mode on `threads` host threads (0: every
+    online core); the same lists as build_knng(count_mode="batched").
+    Returns (ids, dists, stats dict with the threads used)."""
+    data = _f32(data)
+    n, d = data.shape
+    ids = np.empty((n, K), np.int32)
+    dists = np.empty((n, K), np.float32)
+    st = np.zeros(5, np.int64)
+    rc = _load().orc_build_mt(_p(data), n, d, K, rho, delta, max_iters, seed, int(threads), _p(ids), _p(dists),
+                              _p(st))
+    if rc:
+        raise ValueError(f"orc_build_mt failed ({rc})")
+    return ids, dists, dict(iters=int(st[0]), evals=int(st[1]), last_changes=int(st[2]), threads=int(st[4]))
+
+
+def default_threads() -> int:
+    """Host threads build_knng_mt uses by default (the online cores)."""
+    return int(_load().orc_default_threads())
 
 
 class State:

@@ -39,9 +39,11 @@
  * from that definition.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 #define ORC_NEW 1u   /* entry not yet sampled as a "new" forward candidate */
 #define ORC_INS 2u   /* entry inserted during the current iteration        */
@@ -955,6 +957,233 @@ int orc_build(const float *data, int64_t n, int d, int K, float rho, float delta
     if (rc == 0) rc = orc_get_graph(st, ids, dists);
     if (stats) {
         stats[0] = st->iter; stats[1] = evals; stats[2] = last; stats[3] = st->reordered;
+    }
+    orc_free(st);
+    return rc;
+}
+
+/* ------------------------------------------------ batched, multi-thread ---- */
+
+/*
+ * The same NN-Descent in batched mode on several threads.  Reading 6 of the
+ * paper's Section 2 loop: within one iteration the candidate sets are fixed,
+ * so every pair of the calculation step has the same distance whatever the
+ * order, and a list that takes each of its proposals by the update rule of
+ * orc_update ends as the K smallest distinct (dist, id) keys among its entries
+ * and those proposals, in any order.  So this build visits the nodes in blocks
+ * (each block split over the threads by u): the join of a block computes its
+ * pairs and keeps a proposal (p, q, dist) only when (dist, q) orders before
+ * p's current worst entry (one that does not can never enter, since a list's
+ * worst entry only falls); then every thread applies the block's proposals to
+ * the lists of its own range of targets with orc_update.  Selection is
+ * orc_sample (serial) and the change count is the batched one (entries present
+ * after the iteration that were not before), so the result equals orc_build
+ * with count_mode 0, for any number of threads.
+ */
+typedef struct {
+    int32_t p, q;
+    float dist;
+} orc_prop;
+
+typedef struct {
+    orc_prop *a;
+    int64_t len, cap;
+} orc_pvec;
+
+typedef struct {
+    orc_state *st;
+    int threads;
+    int64_t u0, u1;          /* the block */
+    int64_t *next;           /* next node of the block to join (shared) */
+    orc_pvec *buf;           /* threads x threads: [worker][target range] */
+    int64_t evals;           /* this worker's distance evaluations */
+    int64_t ins;             /* this worker's insertions */
+    int worker, fail;
+} orc_work;
+
+static int orc_pvec_push(orc_pvec *v, int32_t p, int32_t q, float dist)
+{
+    if (v->len == v->cap) {
+        int64_t nc = v->cap ? v->cap * 2 : 1024;
+        orc_prop *na = (orc_prop *)realloc(v->a, sizeof(orc_prop) * (size_t)nc);
+        if (!na) return -1;
+        v->a = na;
+        v->cap = nc;
+    }
+    v->a[v->len].p = p;
+    v->a[v->len].q = q;
+    v->a[v->len].dist = dist;
+    v->len++;
+    return 0;
+}
+
+/* target range of node p: [p * threads / n] */
+static int orc_range_of(int64_t p, int64_t n, int threads)
+{
+    return (int)((p * (int64_t)threads) / n);
+}
+
+/* propose q to p when (dist, q) orders before p's worst entry */
+static int orc_propose(orc_work *w, int32_t p, int32_t q, float dist)
+{
+    orc_state *st = w->st;
+    const orc_entry *worst = st->lists + (int64_t)p * st->K + (st->K - 1);
+    orc_entry e = {dist, q, 0u};
+    if (!orc_less(&e, worst)) return 0;
+    return orc_pvec_push(&w->buf[(int64_t)w->worker * w->threads + orc_range_of(p, st->n, w->threads)], p, q, dist);
+}
+
+static void *orc_join_worker(void *arg)
+{
+    orc_work *w = (orc_work *)arg;
+    orc_state *st = w->st;
+    for (;;) {
+        int64_t u = __atomic_fetch_add(w->next, 1, __ATOMIC_RELAXED);
+        if (u >= w->u1) break;
+        const int32_t *nw = st->new_c[u], *od = st->old_c[u];
+        int32_t m = st->new_n[u], o = st->old_n[u];
+        for (int32_t i = 0; i < m; ++i) {
+            for (int32_t j = i + 1; j < m; ++j) {
+                float dd = orc_dist32(st->data, st->d, nw[i], nw[j]);
+                ++w->evals;
+                if (orc_propose(w, nw[i], nw[j], dd) || orc_propose(w, nw[j], nw[i], dd)) { w->fail = 1; return NULL; }
+            }
+            for (int32_t j = 0; j < o; ++j) {
+                float dd = orc_dist32(st->data, st->d, nw[i], od[j]);
+                ++w->evals;
+                if (orc_propose(w, nw[i], od[j], dd) || orc_propose(w, od[j], nw[i], dd)) { w->fail = 1; return NULL; }
+            }
+        }
+    }
+    return NULL;
+}
+
+static void *orc_apply_worker(void *arg)
+{
+    orc_work *w = (orc_work *)arg;
+    for (int src = 0; src < w->threads; ++src) {
+        orc_pvec *v = &w->buf[(int64_t)src * w->threads + w->worker];
+        for (int64_t i = 0; i < v->len; ++i) w->ins += orc_update(w->st, v->a[i].p, v->a[i].q, v->a[i].dist);
+        v->len = 0;
+    }
+    return NULL;
+}
+
+/* pairs per block of orc_join_mt (tests make it small to cross blocks) */
+static int64_t orc_mt_block_pairs = (int64_t)1 << 25;
+
+int orc_set_mt_block_pairs(int64_t pairs)
+{
+    if (pairs < 1) return -1;
+    orc_mt_block_pairs = pairs;
+    return 0;
+}
+
+static int orc_run_workers(orc_work *w, int threads, void *(*fn)(void *))
+{
+    pthread_t *tid = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
+    if (!tid) return -2;
+    int started = 0, rc = 0;
+    for (int t = 1; t < threads; ++t) {
+        if (pthread_create(&tid[t], NULL, fn, &w[t]) != 0) { rc = -2; break; }
+        ++started;
+    }
+    fn(&w[0]);
+    for (int t = 1; t <= started; ++t) pthread_join(tid[t], NULL);
+    free(tid);
+    return rc;
+}
+
+/* One calculation step in batched mode: out as in orc_join. */
+static int orc_join_mt(orc_state *st, int threads, int64_t *out)
+{
+    int64_t n = st->n;
+    orc_work *w = (orc_work *)calloc((size_t)threads, sizeof(orc_work));
+    orc_pvec *buf = (orc_pvec *)calloc((size_t)threads * (size_t)threads, sizeof(orc_pvec));
+    int rc = 0;
+    if (!w || !buf) { free(w); free(buf); return -2; }
+    int64_t next = 0;
+    for (int t = 0; t < threads; ++t) {
+        w[t].st = st;
+        w[t].threads = threads;
+        w[t].buf = buf;
+        w[t].worker = t;
+        w[t].next = &next;
+    }
+    /* blocks of about orc_mt_block_pairs pairs (2^25 by default), so the
+     * kept proposals stay within a few hundred MB */
+    int64_t u0 = 0;
+    while (u0 < n && rc == 0) {
+        int64_t pairs = 0, u1 = u0;
+        while (u1 < n && (u1 == u0 || pairs < orc_mt_block_pairs)) {
+            int64_t m = st->new_n[u1], o = st->old_n[u1];
+            pairs += m * (m - 1) / 2 + m * o;
+            ++u1;
+        }
+        next = u0;
+        for (int t = 0; t < threads; ++t) { w[t].u0 = u0; w[t].u1 = u1; }
+        rc = orc_run_workers(w, threads, orc_join_worker);
+        for (int t = 0; t < threads; ++t) if (w[t].fail) rc = -2;
+        if (rc == 0) rc = orc_run_workers(w, threads, orc_apply_worker);
+        u0 = u1;
+    }
+    int64_t evals = 0, ins = 0;
+    for (int t = 0; t < threads; ++t) { evals += w[t].evals; ins += w[t].ins; }
+    for (int64_t i = 0; i < (int64_t)threads * threads; ++i) free(buf[i].a);
+    free(w);
+    free(buf);
+    if (rc) return rc;
+    int64_t surv = 0;
+    for (int64_t i = 0; i < n * st->K; ++i) {
+        if (st->lists[i].flags & ORC_INS) {
+            ++surv;
+            st->lists[i].flags &= ~ORC_INS;
+        }
+    }
+    out[0] = evals;
+    out[1] = ins;
+    out[2] = surv;
+    return 0;
+}
+
+/* Threads the multi-thread build uses for threads <= 0: the online cores. */
+int orc_default_threads(void)
+{
+    long c = sysconf(_SC_NPROCESSORS_ONLN);
+    return c < 1 ? 1 : (c > 256 ? 256 : (int)c);
+}
+
+/*
+ * Whole NN-Descent, batched mode, on `threads` threads (<= 0: every online
+ * core): the loop of orc_build with count_mode 0 and the calculation step of
+ * orc_join_mt.  Turbosampling, no reordering.  stats as in orc_build, plus
+ * stats[4] = the threads used.
+ */
+int orc_build_mt(const float *data, int64_t n, int d, int K, float rho, float delta,
+                 int max_iters, uint64_t seed, int threads, int32_t *ids, float *dists, int64_t *stats)
+{
+    if (delta < 0.0f || max_iters < 0) return -1;
+    if (threads <= 0) threads = orc_default_threads();
+    if (threads > 256) threads = 256;
+    orc_state *st = orc_create(data, n, d, K, rho, seed);
+    if (!st) return -1;
+    int rc = orc_init_random(st);
+    int64_t evals = 0, last = 0;
+    double thr = (double)delta * (double)n * (double)K;
+    for (int it = 0; rc == 0 && it < max_iters; ++it) {
+        int64_t out[3], sst[3];
+        rc = orc_sample(st, st->iter + 1, sst);
+        if (rc) break;
+        rc = orc_join_mt(st, threads, out);
+        if (rc) break;
+        st->iter++;
+        evals += out[0];
+        last = out[2];
+        if ((double)last < thr) break;
+    }
+    if (rc == 0) rc = orc_get_graph(st, ids, dists);
+    if (stats) {
+        stats[0] = st->iter; stats[1] = evals; stats[2] = last; stats[3] = 0; stats[4] = threads;
     }
     orc_free(st);
     return rc;

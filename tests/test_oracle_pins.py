@@ -542,3 +542,42 @@ def test_build_with_reorder_returns_original_labels():
     assert st["reordered"]
     assert metrics.check_graph(x, ids, dists, rtol=1e-6) == []
     assert metrics.recall(x, ids, ei) >= 0.99
+
+
+# ------------------------------------------- batched build on many threads ----
+
+@pytest.mark.parametrize("threads,block_pairs", [(1, 1 << 25), (3, 1 << 25), (8, 5000), (5, 1)])
+def test_multithread_build_equals_serial_build(threads, block_pairs):
+    """Reading 6 (Section 2 loop, update visibility): with the candidate sets
+    fixed for an iteration, the lists end the same whatever order the
+    proposals are applied in.  The threaded build (blocks of nodes, proposals
+    filtered against the current worst entry, applied per target range) must
+    therefore equal the serial build with the batched change count, bit for
+    bit and with the same number of iterations, for any thread count and any
+    block size (block_pairs 1: one node per block)."""
+    lib = oracle._load()
+    lib.orc_set_mt_block_pairs(block_pairs)
+    try:
+        for (n, d, K, rho, delta, it, seed) in [(1500, 8, 10, 1.0, 0.001, 10, 3), (2500, 12, 12, 0.5, 0.0, 6, 4)]:
+            x = workloads.gaussian_mixture(n, d, clusters=12, seed=seed)
+            a_ids, a_d, a_st = oracle.build_knng(x, K, rho, delta, it, seed=seed, count_mode="batched")
+            b_ids, b_d, b_st = oracle.build_knng_mt(x, K, rho, delta, it, seed=seed, threads=threads)
+            assert b_st["threads"] == threads
+            np.testing.assert_array_equal(a_ids, b_ids)
+            np.testing.assert_array_equal(a_d, b_d)
+            assert (a_st["iters"], a_st["evals"], a_st["last_changes"]) == \
+                (b_st["iters"], b_st["evals"], b_st["last_changes"])
+    finally:
+        lib.orc_set_mt_block_pairs(1 << 25)
+
+
+def test_multithread_build_equals_inplace_lists():
+    """The in-place build (later joins see earlier updates within an
+    iteration, the paper's single-core order) gives the same lists when both
+    run the same iterations (delta = 0): reading 6 against the in-place code."""
+    x = workloads.uniform(1200, 6, seed=8)
+    a_ids, a_d, _ = oracle.build_knng(x, 8, 0.6, 0.0, 7, seed=1, count_mode="inplace")
+    b_ids, b_d, b_st = oracle.build_knng_mt(x, 8, 0.6, 0.0, 7, seed=1, threads=4)
+    assert b_st["iters"] == 7
+    np.testing.assert_array_equal(a_ids, b_ids)
+    np.testing.assert_array_equal(a_d, b_d)

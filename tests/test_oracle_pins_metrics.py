@@ -223,7 +223,7 @@ def _mutant(tmp_path, name):
     path = tmp_path / f"knng_oracle_{name}.c"
     path.write_text(src.replace(old, new))
     lib = tmp_path / f"liboracle_{name}.so"
-    subprocess.run(["gcc", *oracle.CFLAGS, str(path), "-o", str(lib), "-lm"], check=True)
+    subprocess.run(["gcc", *oracle.CFLAGS, str(path), "-o", str(lib), "-lm", "-lpthread"], check=True)
     return oracle._bind(ctypes.CDLL(str(lib)))
 
 
