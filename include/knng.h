@@ -283,20 +283,26 @@ int knng_measure_l2_read(int64_t bytes, int passes, void *stream, double *gbs);
  * callers that must not allocate after start-up.  The paper has no
  * counterpart; it is the same computation as knng_bruteforce.
  *
- * data, ids, dists (and rows, when not NULL) must be device pointers of the
- * current device, with the layouts of knng_bruteforce; the caller owns them.
+ * data, ids, dists (and rows, when not NULL) must be device memory of the
+ * current device (or managed memory it can reach), with the layouts of
+ * knng_bruteforce; the caller owns them.  Host pointers and memory of another
+ * device are refused with KNNG_ERR_INVALID_ARG before anything is launched.
  * The only scratch, the zero-padded copy of the points, is a static device
  * array of KNNG_NOALLOC_SCRATCH_BYTES that every GPU loading the library
  * holds until the process exits.  Returns KNNG_ERR_INVALID_ARG when
- * n * round_up(d, 4) * 4 exceeds KNNG_NOALLOC_SCRATCH_BYTES, or when a
- * pointer is not a device pointer.
+ * n * round_up(d, 4) * 4 exceeds KNNG_NOALLOC_SCRATCH_BYTES.
  *
- * The first call on a device looks up the array's device address (one
- * cudaGetSymbolAddress, no allocation); make that first call before any
- * stream capture.  All calls share the one array and it keeps the last call's
- * contents; each call overwrites the whole region it reads before reading it.
- * Calls whose work overlaps on the GPU (other streams, other threads) race on
- * the array: serialise them.  Enqueues on `stream`, does not synchronise.
+ * The first call in a CUDA context (the first on a device, and the first
+ * after a device reset, which makes a new context) does a set-up that
+ * allocates nothing: it looks up the array's device address (one
+ * cudaGetSymbolAddress), loads every kernel the call can use and opts them in
+ * to their shared memory.  Make that first call before any stream capture;
+ * later calls only enqueue kernels (rows of more than 16,384 floats may still
+ * set a kernel's shared-memory attribute on their first call).  All calls share the one array and it
+ * keeps the last call's contents; each call overwrites the whole region it
+ * reads before reading it.  Calls whose work overlaps on the GPU (other
+ * streams, other threads) race on the array: serialise them.  Enqueues on
+ * `stream`, does not synchronise.
  */
 #define KNNG_NOALLOC_SCRATCH_BYTES (8u << 20)
 int knng_bruteforce_noalloc(const float *data, int64_t n, int d, int K, const int64_t *rows,

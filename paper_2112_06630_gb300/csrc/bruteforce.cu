@@ -11,6 +11,8 @@
 // keys).  Distances use the library's canonical float32 difference form, so
 // ground truth and NN-Descent agree on the value of every pair.
 #include <algorithm>
+#include <cstdlib>
+#include <map>
 #include <mutex>
 
 #include "../../include/knng.h"
@@ -180,6 +182,34 @@ cudaError_t launch_bruteforce(const float *X, int64_t n, int dp, int K, const in
     return launch_bf_k<32>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
 }
 
+namespace {
+template <int KMAX, int NVR>
+cudaError_t prepare_bf_t() {
+    cudaFuncAttributes a;
+    auto kern = bruteforce_kernel<KMAX, NVR>;
+    cudaError_t e = cudaFuncGetAttributes(&a, kern);
+    if (e == cudaSuccess) e = smem_opt_in((const void *)kern, kBfSmem);
+    return e;
+}
+template <int KMAX>
+cudaError_t prepare_bf_k() {
+    cudaError_t e = prepare_bf_t<KMAX, 2>();
+    if (e == cudaSuccess) e = prepare_bf_t<KMAX, 4>();
+    if (e == cudaSuccess) e = prepare_bf_t<KMAX, 8>();
+    if (e == cudaSuccess) e = prepare_bf_t<KMAX, 0>();
+    return e;
+}
+}  // namespace
+
+cudaError_t prepare_bruteforce_one_slice() {
+    cudaError_t e = prepare_stage();
+    if (e == cudaSuccess) e = prepare_bf_k<8>();
+    if (e == cudaSuccess) e = prepare_bf_k<16>();
+    if (e == cudaSuccess) e = prepare_bf_k<24>();
+    if (e == cudaSuccess) e = prepare_bf_k<32>();
+    return e;
+}
+
 }  // namespace knng
 
 // ---------------------------------------------------------------------------
@@ -192,35 +222,45 @@ cudaError_t launch_bruteforce(const float *X, int64_t n, int dp, int K, const in
 static __device__ __align__(256) float knng_noalloc_points[KNNG_NOALLOC_SCRATCH_BYTES / sizeof(float)];
 
 namespace {
-constexpr int kNoAllocMaxDevices = 256;
-float *g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
 std::mutex g_noalloc_mu;
+std::map<unsigned long long, float *> g_noalloc_addr;  // device address of the array, per context
 
-// Device address of the scratch array on the current device.  Looked up once
-// per device (host code cannot use the array's name as a device address).
+// Set-up, once per context (the first call on a device, and the first after
+// a device reset): the array's device address -- host code cannot use its
+// name as one -- and every kernel of the path loaded and opted in to the
+// shared memory it may use, so that later calls, captured ones included, do
+// neither.
 cudaError_t noalloc_scratch(float **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    unsigned long long ctx = 0;
+    cudaError_t e = knng::current_context_id(&ctx);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    auto it = g_noalloc_addr.find(ctx);
+    if (it == g_noalloc_addr.end()) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, knng_noalloc_points);
         if (e != cudaSuccess) return e;
-        g_noalloc_addr[dev] = static_cast<float *>(p);
+        e = knng::prepare_bruteforce_one_slice();
+        if (e != cudaSuccess) return e;
+        it = g_noalloc_addr.emplace(ctx, static_cast<float *>(p)).first;
     }
-    *out = g_noalloc_addr[dev];
+    *out = it->second;
     return cudaSuccess;
 }
 
-bool noalloc_on_device(const void *p) {
+// True when the kernels of device `dev` may dereference p: device memory of
+// that device, or managed memory it can reach (its own, or any when it
+// accesses managed memory concurrently).  Host memory and other devices'
+// memory are refused before anything is launched.
+bool noalloc_pointer_ok(const void *p, int dev, int concurrent_managed) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+    if (a.type == cudaMemoryTypeManaged) return a.device == dev || concurrent_managed != 0;
+    return false;
 }
 }  // namespace
 
@@ -233,12 +273,30 @@ extern "C" int knng_bruteforce_noalloc(const float *data, int64_t n, int d, int 
         return KNNG_ERR_INVALID_ARG;
     if (!rows) nq = n;
     if (nq < 1) return KNNG_ERR_INVALID_ARG;
-    if (!noalloc_on_device(data) || !noalloc_on_device(ids) || !noalloc_on_device(dists) ||
-        (rows && !noalloc_on_device(rows)))
+    int dev = 0, cma = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return KNNG_ERR_CUDA;
+    }
+    if (cudaDeviceGetAttribute(&cma, cudaDevAttrConcurrentManagedAccess, dev) != cudaSuccess) {
+        cudaGetLastError();
+        cma = 0;
+    }
+    // test hook: check the pointers as if another device were current (every
+    // device pointer then belongs to a foreign device), with nothing launched
+    if (std::getenv("KNNG_TEST_NOALLOC_FOREIGN_DEVICE")) {
+        dev += 1;
+        cma = 0;
+    }
+    if (!noalloc_pointer_ok(data, dev, cma) || !noalloc_pointer_ok(ids, dev, cma) ||
+        !noalloc_pointer_ok(dists, dev, cma) || (rows && !noalloc_pointer_ok(rows, dev, cma)))
         return KNNG_ERR_INVALID_ARG;
     float *X = nullptr;
     cudaError_t e = noalloc_scratch(&X);
-    if (e != cudaSuccess) return KNNG_ERR_CUDA;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return KNNG_ERR_CUDA;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // staging writes every element of the n x dp region it uses (padding
     // included), so nothing left by an earlier call is read

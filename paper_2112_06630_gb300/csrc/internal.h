@@ -11,11 +11,15 @@ namespace knng {
 
 // persistent grid size for a warp-per-item kernel: a multiple of the SM count
 int grid_for(const void *kernel, int block_threads, size_t dyn_smem);
-// opt `kernel` in to `bytes` of dynamic shared memory on the current device
-// (once per kernel, device and size; thread-safe)
+// opt `kernel` in to `bytes` of dynamic shared memory in the current context
+// (once per kernel, context and size; thread-safe)
 cudaError_t smem_opt_in(const void *kernel, size_t bytes);
+// id of the calling thread's current CUDA context (new after a device reset)
+cudaError_t current_context_id(unsigned long long *id);
 
 cudaError_t launch_stage(const float *src, int64_t n, int d, float *X, int dp, cudaStream_t s);
+// load stage_kernel in the current context
+cudaError_t prepare_stage();
 cudaError_t launch_init_random(const DevState &st, uint64_t seed, int *err, cudaStream_t s);
 cudaError_t launch_init_graph(const DevState &st, const int32_t *ids, const uint8_t *is_new, int *err,
                               cudaStream_t s);
@@ -59,6 +63,10 @@ cudaError_t launch_invert(const int32_t *perm, int64_t n, int32_t *inv, cudaStre
 // null for one slice (no scratch)
 cudaError_t launch_bruteforce(const float *X, int64_t n, int dp, int K, const int64_t *rows, int64_t nq,
                               int32_t *ids, float *dists, cudaStream_t s, uint64_t *part, int S);
+// load every kernel launch_stage and a one-slice launch_bruteforce can use and
+// opt them in to the shared memory they may ask for, in the current context,
+// so that later launches neither load code nor set attributes
+cudaError_t prepare_bruteforce_one_slice();
 // slices that give every SM work for nq queries over n points
 int bruteforce_slices(int64_t n, int64_t nq);
 // tensor-core brute force (bf16 split Gram prefilter, exact re-rank, exact

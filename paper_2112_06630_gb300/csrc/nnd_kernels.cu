@@ -30,18 +30,62 @@ int grid_for(const void *kernel, int block_threads, size_t dyn_smem) {
     return sms * per_sm;
 }
 
-// Dynamic shared memory above the 48 KB default needs a per-function opt-in,
-// and the attribute belongs to the current device's context: record the
-// largest size granted per (kernel, device) under a lock.
+// Id of the calling thread's current CUDA context, from the driver's
+// cuCtxGetCurrent and cuCtxGetId (looked up once through the runtime, so the
+// library needs no link against the driver).  A context made after a device
+// reset gets a new id, so state cached per id never outlives its context.
+cudaError_t current_context_id(unsigned long long *id) {
+    typedef int (*GetCurrentFn)(void **);
+    typedef int (*GetIdFn)(void *, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrentFn>(a);
+            get_id = reinterpret_cast<GetIdFn>(b);
+        } else {
+            cudaGetLastError();
+        }
+    });
+    if (!get_current || !get_id) return cudaErrorNotSupported;
+    void *ctx = nullptr;
+    if (get_current(&ctx) == 0 && !ctx) {
+        // a thread that has not used the runtime yet: bind the current
+        // device's primary context
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaSetDevice(dev);
+        if (e != cudaSuccess) return e;
+        ctx = nullptr;
+        get_current(&ctx);
+    }
+    if (!ctx) return cudaErrorDeviceUninitialized;
+    return get_id(ctx, id) == 0 ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Dynamic shared memory above the 48 KB default needs a per-function opt-in.
+// The attribute belongs to the current context: record the largest size
+// granted per (kernel, context) under a lock (a context made after a device
+// reset starts without any grant).
 cudaError_t smem_opt_in(const void *kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+    unsigned long long ctx = 0;
+    cudaError_t e = current_context_id(&ctx);
+    if (e != cudaSuccess) {
+        // no context id: set the attribute every time
+        cudaGetLastError();
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    }
     static std::mutex mu;
-    static std::map<std::pair<const void *, int>, size_t> granted;
+    static std::map<std::pair<const void *, unsigned long long>, size_t> granted;
     std::lock_guard<std::mutex> g(mu);
-    size_t &have = granted[{kernel, dev}];
+    size_t &have = granted[{kernel, ctx}];
     if (have >= bytes) return cudaSuccess;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) have = bytes;
@@ -64,6 +108,13 @@ cudaError_t launch_stage(const float *src, int64_t n, int d, float *X, int dp, c
     int grid = grid_for((const void *)stage_kernel, 256, 0);
     stage_kernel<<<grid, 256, 0, s>>>(src, n, d, X, dp);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_stage() {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, stage_kernel);
+    if (e == cudaSuccess) grid_for((const void *)stage_kernel, 256, 0);
+    return e;
 }
 
 // ------------------------------------------------------------ random init ----

@@ -78,3 +78,68 @@ def test_noalloc_rejects_oversize_and_host_pointers(noalloc):
     ids = np.zeros((100, 4), np.int32)
     dists = np.zeros((100, 4), np.float32)
     assert noalloc(xh.ctypes.data, 100, 4, 4, None, 100, ids.ctypes.data, dists.ctypes.data, None) == -1
+
+
+def test_noalloc_scratch_exactly_full_and_just_under(noalloc):
+    """The size limit at its edge: a padded copy that fills the array exactly
+    (16 floats x 131,072 rows = 8 MiB) is taken, and so is a row width that
+    is not a multiple of 4 just under it (7 floats pad to 8: 262,143 rows);
+    one row more is refused.  Query rows keep the runs short."""
+    g = np.random.default_rng(5)
+    for n, d in ((SCRATCH_BYTES // (4 * 16), 16), (SCRATCH_BYTES // (4 * 8) - 1, 7)):
+        x = workloads.gaussian_mixture(n, d, 64, seed=d)
+        xd = torch.from_numpy(x).cuda()
+        rows = torch.from_numpy(np.sort(g.choice(n, 40, replace=False)).astype(np.int64)).cuda()
+        rc, gi, gd = _call(noalloc, xd, 12, rows)
+        assert rc == 0
+        ri, rd = knng.knng_bruteforce(xd, 12, rows=rows)
+        _same_up_to_ties(gi, gd, ri.cpu().numpy(), rd.cpu().numpy())
+    big = torch.zeros((SCRATCH_BYTES // (4 * 8) + 1, 7), dtype=torch.float32, device="cuda")
+    rc, _, _ = _call(noalloc, big, 4, torch.zeros(1, dtype=torch.int64, device="cuda"))
+    assert rc == -1
+
+
+def test_noalloc_refuses_foreign_device_memory(noalloc, monkeypatch):
+    """Memory of another device is refused before any launch.  With one GPU
+    the test hook makes the library check the pointers as if another device
+    were current: every device pointer then belongs to a foreign device."""
+    xd = torch.from_numpy(workloads.uniform(300, 8, seed=3)).cuda()
+    monkeypatch.setenv("KNNG_TEST_NOALLOC_FOREIGN_DEVICE", "1")
+    rc, gi, _ = _call(noalloc, xd, 5)
+    assert rc == -1 and (gi == -1).all()
+    monkeypatch.delenv("KNNG_TEST_NOALLOC_FOREIGN_DEVICE")
+    rc, gi, _ = _call(noalloc, xd, 5)
+    assert rc == 0 and (gi >= 0).all()
+
+
+def test_noalloc_inside_global_mode_capture(noalloc):
+    """The case the entry point exists for: calls recorded while a stream is
+    captured in global mode (where an allocation would fail the capture).
+    One eager call first does the per-context set-up; the captured calls then
+    use other K classes and row paths than that call (K 20 over 64-float rows,
+    whose tiles need more than 48 KB of shared memory, and K 30 over 7-float
+    rows).  The replayed graph gives knng_bruteforce's answers."""
+    warm = torch.from_numpy(workloads.uniform(500, 8, seed=4)).cuda()
+    assert _call(noalloc, warm, 4)[0] == 0
+    cases = [(workloads.gaussian_mixture(3000, 64, 20, seed=6), 20), (workloads.uniform(2500, 7, seed=7), 30)]
+    ins, outs = [], []
+    for x, K in cases:
+        xd = torch.from_numpy(x).cuda()
+        ins.append((xd, K))
+        outs.append((torch.full((x.shape[0], K), -1, dtype=torch.int32, device="cuda"),
+                     torch.full((x.shape[0], K), -1.0, dtype=torch.float32, device="cuda")))
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    rcs = []
+    with torch.cuda.graph(graph, capture_error_mode="global"):
+        s = torch.cuda.current_stream().cuda_stream
+        for (xd, K), (ids, dists) in zip(ins, outs):
+            rcs.append(noalloc(xd.data_ptr(), xd.shape[0], xd.shape[1], K, None, xd.shape[0], ids.data_ptr(),
+                               dists.data_ptr(), s))
+    assert rcs == [0, 0]
+    assert all((ids == -1).all() for ids, _ in outs)  # captured, not yet run
+    graph.replay()
+    torch.cuda.synchronize()
+    for (xd, K), (ids, dists) in zip(ins, outs):
+        ri, rd = knng.knng_bruteforce(xd, K)
+        _same_up_to_ties(ids.cpu().numpy(), dists.cpu().numpy(), ri.cpu().numpy(), rd.cpu().numpy())
