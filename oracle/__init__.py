@@ -50,6 +50,7 @@ _SIGS = {
     "orc_sample_heap": (_i32, [P_, _i32, P_]),
     "orc_set_sampler": (_i32, [P_, _i32]),
     "orc_join": (_i32, [P_, P_]),
+    "orc_join_range": (_i32, [P_, _i64, _i64, P_]),
     "orc_iterate": (_i32, [P_, P_]),
     "orc_reorder": (_i32, [P_, _i32]),
     "orc_get_samples": (_i32, [P_, _i32, P_, P_, P_, P_]),
@@ -245,6 +246,13 @@ class State:
         out = np.zeros(3, np.int64)
         self._lib.orc_join(self._h, _p(out))
         return dict(evals=int(out[0]), inserts=int(out[1]), changes=int(out[2]))
+
+    def join_range(self, u0: int, u1: int):
+        """Calculation step of nodes u0 <= u < u1 only (for timing a bounded
+        share of an iteration): distance evaluations and insertions."""
+        out = np.zeros(2, np.int64)
+        self._lib.orc_join_range(self._h, int(u0), int(u1), _p(out))
+        return dict(evals=int(out[0]), inserts=int(out[1]))
 
     def iterate(self):
         out = np.zeros(6, np.int64)

@@ -576,6 +576,38 @@ static int orc_update(orc_state *st, int32_t p, int32_t q, float dist)
  * count), out[2] = entries present after the step that were not present before
  * it (batched count).
  */
+/* The calculation step of nodes u0 <= u < u1 only (out[0] evaluations,
+ * out[1] insertions; the change count is left to a whole step).  For timing
+ * a bounded share of an iteration. */
+int orc_join_range(orc_state *st, int64_t u0, int64_t u1, int64_t *out)
+{
+    int64_t evals = 0, ins = 0;
+    if (u0 < 0) u0 = 0;
+    if (u1 > st->n) u1 = st->n;
+    for (int64_t u = u0; u < u1; ++u) {
+        const int32_t *nw = st->new_c[u];
+        const int32_t *od = st->old_c[u];
+        int32_t m = st->new_n[u], o = st->old_n[u];
+        for (int32_t i = 0; i < m; ++i) {
+            for (int32_t j = i + 1; j < m; ++j) {
+                float dd = orc_dist32(st->data, st->d, nw[i], nw[j]);
+                ++evals;
+                ins += orc_update(st, nw[i], nw[j], dd);
+                ins += orc_update(st, nw[j], nw[i], dd);
+            }
+            for (int32_t j = 0; j < o; ++j) {
+                float dd = orc_dist32(st->data, st->d, nw[i], od[j]);
+                ++evals;
+                ins += orc_update(st, nw[i], od[j], dd);
+                ins += orc_update(st, od[j], nw[i], dd);
+            }
+        }
+    }
+    out[0] = evals;
+    out[1] = ins;
+    return 0;
+}
+
 int orc_join(orc_state *st, int64_t *out)
 {
     int64_t n = st->n;

@@ -581,3 +581,19 @@ def test_multithread_build_equals_inplace_lists():
     assert b_st["iters"] == 7
     np.testing.assert_array_equal(a_ids, b_ids)
     np.testing.assert_array_equal(a_d, b_d)
+
+
+def test_join_range_halves_make_the_whole_step():
+    """The calculation step of two node ranges in turn is the whole step: the
+    same evaluations and (reading 6) the same lists."""
+    x = workloads.uniform(1500, 6, seed=2)
+    a = oracle.State(x, 8, 0.7, seed=3)
+    b = oracle.State(x, 8, 0.7, seed=3)
+    for s in (a, b):
+        s.init_random()
+        s.sample(1)
+    whole = a.join()
+    h1, h2 = b.join_range(0, 700), b.join_range(700, 1500)
+    assert h1["evals"] + h2["evals"] == whole["evals"]
+    np.testing.assert_array_equal(a.state()[0], b.state()[0])
+    np.testing.assert_array_equal(a.state()[1], b.state()[1])
