@@ -101,8 +101,10 @@ typedef struct knng_stats {
     int32_t join_launches;     /* local-join launches timed (KNNG_FLAG_TIMING) */
     double join_ms;            /* their summed CUDA-event time */
     int32_t join_ran;          /* timed launches whose iteration ran (not skipped) */
-    int32_t join_path;         /* local-join kernel: 0 warp per node (float32 rows of up to 64
-                                  floats), 1 block-per-node tiles, 2 TMA-staged ring */
+    int32_t join_path;         /* local-join kernel: 0 warp per node (float32 rows of up to 32
+                                  floats), 1 block-per-node tiles, 2 ring of nodes in flight
+                                  (bf16 rows), 3 pipelined block per node (float32 rows of 33
+                                  to 256 floats) */
     double join_ms_ran;        /* summed join-kernel time of those iterations */
     double merge_ms_ran;       /* summed list-merge-kernel time of those iterations */
     double sample_ms_ran;      /* summed selection-step time (degree count + sampling kernels) of

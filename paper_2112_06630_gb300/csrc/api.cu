@@ -240,8 +240,9 @@ int ctx_alloc(knng_ctx *c) {
     const size_t oE = take(sizeof(int));
     const size_t oXb = c->bf16 ? take(sizeof(uint16_t) * n * c->dpb) : 0;
     const size_t oXn = c->bf16 ? take(sizeof(float) * n) : 0;
-    const bool ring = c->join_path == kJoinRing ||
-                      (c->tune_pending && ring_join_fits(c->bf16, c->nv, c->dpb, c->K));
+    const bool ring = c->join_path == kJoinRing || c->join_path == kJoinPipe ||
+                      (c->tune_pending && (ring_join_fits(c->bf16, c->nv, c->dpb, c->K) ||
+                                           pipe_join_fits(c->bf16, c->nv)));
     const size_t oCs = ring ? take(sizeof(int) * (size_t)n * kSetMax) : 0;
     const size_t oCm = ring ? take(sizeof(int) * (size_t)n) : 0;
     const bool prel = reorder && (c->flags & KNNG_FLAG_REORDER_PARALLEL);
@@ -368,6 +369,7 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
         if (!std::strcmp(e, "warp")) force = kJoinWarp;
         else if (!std::strcmp(e, "tile")) force = kJoinTile;
         else if (!std::strcmp(e, "ring")) force = kJoinRing;
+        else if (!std::strcmp(e, "pipe")) force = kJoinPipe;
     }
     c->join_path = choose_join_path(c->bf16, c->nv, c->dpb, K, force);
     if ((flags & KNNG_FLAG_AUTOTUNE) && force < 0) {
@@ -449,6 +451,7 @@ int autotune_join(knng_ctx *c, int li) {
     std::vector<int> paths = {kJoinTile};
     if (!c->bf16) paths.push_back(kJoinWarp);
     if (ring_join_fits(c->bf16, c->nv, c->dpb, c->K) && c->cset) paths.push_back(kJoinRing);
+    if (pipe_join_fits(c->bf16, c->nv) && c->cset) paths.push_back(kJoinPipe);
     const size_t kb = sizeof(uint64_t) * (size_t)c->n * c->K;
     unsigned char *tmp = nullptr;
     KNNG_TRY(lib_malloc((void **)&tmp, align256(kb) + sizeof(long long) * kStatCount, c->stream));

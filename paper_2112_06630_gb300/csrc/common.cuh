@@ -216,15 +216,15 @@ struct DevState {
     const double *ds_thr;      // data set -> delta * n * K
     long long *ds_changes;     // data set x kMaxLocalIters change counts
     double thr;                // delta * n * K
-    // ring join path only (else null): per-node candidate sets written by the
-    // set kernel and read by the ring kernel
+    // ring and pipelined join paths only (else null): per-node candidate sets
+    // written by the set kernel and read by the join kernel
     int *cset;                 // n x 64 candidate ids, new ones first
     int *cmeta;                // n: ns | m << 8 (0: no join pair)
     int join_path;             // JoinPath chosen for this context
 };
 
 // Which local-join kernel a context uses (fixed at creation).
-enum JoinPath : int { kJoinWarp = 0, kJoinTile = 1, kJoinRing = 2 };
+enum JoinPath : int { kJoinWarp = 0, kJoinTile = 1, kJoinRing = 2, kJoinPipe = 3 };
 
 // Proposal buckets: run 0 of node p is inline (pbucket), runs 1..15 are pool
 // chunks claimed on demand with a CAS (a lane that loses the race uses the

@@ -37,6 +37,12 @@ cudaError_t launch_join(const DevState &st, int li, cudaStream_t s);
 cudaError_t launch_merge(const DevState &st, int li, cudaStream_t s);
 cudaError_t launch_tile_join(const DevState &st, int li, bool bf16, cudaStream_t s);
 cudaError_t launch_ring_join(const DevState &st, int li, cudaStream_t s);
+// the set kernel alone: every node's candidate set (repeats removed, new
+// first) into cset / cmeta, for the ring and pipelined join kernels
+cudaError_t launch_set_kernel(const DevState &st, int li, cudaStream_t s);
+// pipelined block join (float32 rows of 33 to 256 floats): set kernel + join
+cudaError_t launch_pipe_join(const DevState &st, int li, cudaStream_t s);
+bool pipe_join_fits(int bf16, int nv);
 // true when a node with 64 candidates fits the ring of the ring join kernel
 bool ring_join_fits(int bf16, int nv, int dpb, int K);
 // true when the ring holds several typical nodes (the default choice)

@@ -1,0 +1,486 @@
+// pipe_join.cu -- the local join (the paper's Calculation step, Section 2;
+// blocked mutual distances of a bounded neighbourhood, Section 3.3) for
+// float32 rows of 33 to 256 floats, as a software pipeline over nodes in
+// which all warps of a block work on one node at a time.
+//
+// The set kernel (ring_join.cu) has written each node's candidate set
+// (repeats removed, new first, at most 64) to cset / cmeta.  Each block of
+// pipe_join_kernel (persistent; one or two per SM) walks the nodes
+// u = blockIdx.x, blockIdx.x + gridDim.x, ...:
+//   producer warp: for every node with a join pair it takes a free row slot
+//     (two per block), writes the ids into it and issues asynchronous copies
+//     of the candidate rows (one 16-byte cp.async per lane, a whole 512-byte
+//     row per warp instruction, rows on an odd number of 16-byte units so
+//     that consecutive rows start on different banks) and of each
+//     candidate's worst-key snapshot; the copies arrive on the slot's
+//     mbarrier, so the next node's rows land while the current one is
+//     computed;
+//   compute warps (eight, together on the current node):
+//     1. the distance block D[i][j] of the new rows i against all rows j, in
+//        the canonical float32 difference form (bit-identical to every other
+//        float32 distance of the library), register-blocked RB rows x 4
+//        columns per thread, RB chosen per node (2 or 1) so that small
+//        nodes still spread over the block; then the row slot is released
+//        to the producer;
+//     2. proposal masks: element (i, j) carries j to i (j != i) and, for an
+//        old j, i to j -- every proposal of the node's join pairs once -- kept
+//        when its key orders before the target's snapshot worst entry;
+//     3. bucket runs: one lane per target reserves the target's range (one
+//        atomicAdd) and claims the pool chunks it spans; every thread then
+//        writes proposals flattened over the block (target by a binary search
+//        over the per-target prefix counts, partner as the r-th set bit of
+//        the target's mask); a proposal whose run has no slot (bucket or pool
+//        spent) is inserted into the list under the list's lock.
+// The proposals are those of the other join kernels, so the lists after the
+// merge are the same bit for bit.  Every wait is bounded by the global timer;
+// a wait that gives up raises the timeout counter and the block winds down
+// once the copies it issued have landed (again a bounded wait).
+#include <cstdint>
+
+#include "join_common.cuh"
+
+namespace knng {
+
+namespace {
+constexpr int kPipeWarps = 8;                       // compute warps
+constexpr int kPipeCompute = 32 * kPipeWarps;       // compute threads
+constexpr int kPipeThreads = kPipeCompute + 32;     // + the producer warp
+constexpr int kPipeSlots = 2;
+constexpr int kPipeMaxUnits = 64;                   // 16-byte units per row: rows of up to 256 floats
+constexpr uint32_t kPipeHdrBytes = 1024;            // slot header: ns, m | ids[64] | worst keys[64]
+constexpr int kPipeDStride = kSetMax + 1;
+constexpr unsigned long long kPipeWaitNs = 2000000000ull;  // 2 s
+
+// Row layout in a slot: column block cb (32 units = 128 floats) holds every
+// row's units [32 cb, 32 cb + 32) on a stride of (units | 1) 16-byte units.
+struct PipeGeo {
+    int nv;                 // 16-byte units per row
+    int nblk;               // column blocks
+    uint32_t stride[2];     // bytes per row in each block
+    uint32_t off[2];        // byte offset of each block in the slot's row area
+    uint32_t rows_bytes;    // the row area
+    uint32_t slot_bytes;    // header + row area
+};
+__host__ __device__ __forceinline__ PipeGeo pipe_geo(int nv) {
+    PipeGeo g;
+    g.nv = nv;
+    g.nblk = (nv + 31) / 32;
+    uint32_t off = 0;
+    for (int cb = 0; cb < 2; ++cb) {
+        const int units = cb < g.nblk ? (nv - 32 * cb < 32 ? nv - 32 * cb : 32) : 0;
+        g.stride[cb] = (uint32_t)(units | 1) * 16u;
+        g.off[cb] = off;
+        if (cb < g.nblk) off += (uint32_t)kSetMax * g.stride[cb];
+    }
+    g.rows_bytes = off;
+    g.slot_bytes = kPipeHdrBytes + ((off + 127u) & ~127u);
+    return g;
+}
+
+// Per-node scratch of the compute warps.
+struct PipeCur {
+    int sid[kSetMax];
+    uint64_t swk[kSetMax];
+    unsigned long long mask[kSetMax];
+    unsigned long long fails[kSetMax];
+    int incl[kSetMax];          // inclusive prefix counts of proposals per target
+    int rbase[kSetMax];         // reserved start minus exclusive prefix
+    unsigned failed[2];         // targets with a proposal that found no slot
+    int total;
+    float D[kSetMax * kPipeDStride];
+};
+
+struct PipeShared {
+    uint64_t full[kPipeSlots];
+    uint64_t empty[kPipeSlots];
+    int abort_flag;
+    long long stat[8];
+};
+
+__host__ __device__ __forceinline__ size_t pipe_smem_bytes(int nv) {
+    const PipeGeo g = pipe_geo(nv);
+    return 128 + (size_t)kPipeSlots * g.slot_bytes + ((sizeof(PipeCur) + 127) & ~(size_t)127);
+}
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t *b) {
+    asm volatile("{\n\t.reg .b64 s;\n\tmbarrier.arrive.shared::cta.b64 s, [%0];\n\t}" ::"r"(su32(b)) : "memory");
+}
+// arrives on the barrier once all of this thread's earlier cp.async copies
+// have landed (counted in the barrier's expected arrivals)
+__device__ __forceinline__ void bar_arrive_copies(uint64_t *b) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase of the given parity; false when it gave up or
+// the block is aborting
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
+    const unsigned long long t0 = gtimer();
+    while (!bar_try(b, parity)) {
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > kPipeWaitNs) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void cpa16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+// named barrier of the compute warps only
+__device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kPipeCompute) : "memory"); }
+
+// float4 unit v of row r in a slot's row area
+__device__ __forceinline__ const float4 *pipe_unit(const unsigned char *rows, const PipeGeo &g, int r, int v) {
+    const int cb = v >> 5;
+    return reinterpret_cast<const float4 *>(rows + g.off[cb] + (uint32_t)r * g.stride[cb] + (uint32_t)(v & 31) * 16u);
+}
+
+// Distance block of the new rows against all rows, RB rows x 4 columns per
+// item: rows a + r MA, columns b + q NB (consecutive threads take consecutive
+// b: consecutive rows, distinct banks; the RB rows are shared by a warp).
+template <int RB>
+__device__ __forceinline__ void pipe_dist(const unsigned char *rows, const PipeGeo &g, float *D, int ns, int m,
+                                          int tid) {
+    const int MA = (m + RB - 1) / RB, NB = (ns + 3) >> 2, items = MA * NB;
+    const uint32_t nbm = div_magic((uint32_t)NB);
+    for (int e = tid; e < items; e += kPipeCompute) {
+        const int a = (int)div_small((uint32_t)e, (uint32_t)NB, nbm), b = e - a * NB;
+        int ri[RB], cj[4];
+        bool vr[RB], vc[4];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            ri[r] = a + r * MA;
+            vr[r] = ri[r] < m;
+            if (!vr[r]) ri[r] = a;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            cj[q] = b + q * NB;
+            vc[q] = cj[q] < ns;
+            if (!vc[q]) cj[q] = b;
+        }
+        Acc4 acc[RB][4];
+        for (int cb = 0; cb < g.nblk; ++cb) {
+            const unsigned char *base = rows + g.off[cb];
+            const uint32_t st = g.stride[cb];
+            const int units = g.nv - 32 * cb < 32 ? g.nv - 32 * cb : 32;
+            const float4 *pr[RB], *pc[4];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) pr[r] = reinterpret_cast<const float4 *>(base + (uint32_t)ri[r] * st);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pc[q] = reinterpret_cast<const float4 *>(base + (uint32_t)cj[q] * st);
+            for (int v = 0; v < units; ++v) {
+                float4 x[RB], y[4];
+#pragma unroll
+                for (int r = 0; r < RB; ++r) x[r] = pr[r][v];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) y[q] = pc[q][v];
+#pragma unroll
+                for (int r = 0; r < RB; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[r][q].add(x[r], y[q]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (vr[r] && vc[q]) D[ri[r] * kPipeDStride + cj[q]] = acc[r][q].sum();
+    }
+}
+}  // namespace
+
+__global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st, int li) {
+    if (iteration_skipped(st, li)) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    PipeShared *sh = reinterpret_cast<PipeShared *>(smem);
+    const PipeGeo geo = pipe_geo(st.nv);
+    unsigned char *slots = smem + 128;
+    PipeCur *cur = reinterpret_cast<PipeCur *>(slots + (size_t)kPipeSlots * geo.slot_bytes);
+    volatile int *abort_flag = &sh->abort_flag;
+    const int tid = threadIdx.x;
+    const unsigned lane = lane_id();
+    const int warp = tid >> 5;
+    const int K = st.K;
+    if (tid == 0) {
+        for (int s = 0; s < kPipeSlots; ++s) {
+            bar_init(&sh->full[s], 33);  // 32 copy arrivals of the producer lanes + its release arrive
+            bar_init(&sh->empty[s], 1);  // the compute warps, once the rows are read
+        }
+        sh->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < 8) sh->stat[tid] = 0;
+    __syncthreads();
+
+    long long w_to = 0;
+    if (warp == kPipeWarps) {
+        // ------------------------------------------------------- producer --
+        int k = 0;  // nodes handed out
+        bool ok = true;
+        // the next node of this block with a join pair (ids in registers)
+        long long u = blockIdx.x;
+        auto next_node = [&](long long from, int &meta, int &id0, int &id1) -> long long {
+            for (long long v = from; v < st.n; v += gridDim.x) {
+                meta = __ldg(st.cmeta + v);
+                if (meta & 0xFF) {
+                    const int ns = meta & 0xFF;
+                    id0 = (int)lane < ns ? __ldg(st.cset + (size_t)v * kSetMax + lane) : 0;
+                    id1 = (int)lane + 32 < ns ? __ldg(st.cset + (size_t)v * kSetMax + 32 + lane) : 0;
+                    return v;
+                }
+            }
+            return st.n;
+        };
+        int meta = 0, id0 = 0, id1 = 0;
+        u = next_node(u, meta, id0, id1);
+        const unsigned char *X = reinterpret_cast<const unsigned char *>(st.X);
+        const size_t row_bytes = (size_t)st.nv * 16;
+        for (;;) {
+            const int slot = k & 1;
+            unsigned char *sb = slots + (size_t)slot * geo.slot_bytes;
+            if (k >= kPipeSlots && !bar_wait(&sh->empty[slot], ((k >> 1) - 1) & 1, abort_flag)) {
+                ok = false;
+                break;
+            }
+            int *hdr = reinterpret_cast<int *>(sb);
+            int *sid = hdr + 4;
+            uint64_t *swk = reinterpret_cast<uint64_t *>(sb + 16 + 4 * kSetMax);
+            if (u >= st.n) {
+                // end mark: no rows; the copy arrivals complete at once
+                if (lane == 0) hdr[0] = 0;
+                __syncwarp();
+                bar_arrive_copies(&sh->full[slot]);
+                if (lane == 0) bar_arrive(&sh->full[slot]);
+                ++k;
+                break;
+            }
+            const int ns = meta & 0xFF, m = (meta >> 8) & 0xFF;
+            if (lane == 0) {
+                hdr[0] = ns;
+                hdr[1] = m;
+            }
+            if ((int)lane < ns) sid[lane] = id0;
+            if ((int)lane + 32 < ns) sid[lane + 32] = id1;
+            // rows: lane l copies units l, l + 32 of every row
+            const uint32_t rows_s = su32(sb + kPipeHdrBytes);
+            for (int r = 0; r < ns; ++r) {
+                const int id = __shfl_sync(kFull, r < 32 ? id0 : id1, r & 31);
+                const unsigned char *src = X + (size_t)id * row_bytes;
+#pragma unroll
+                for (int cb = 0; cb < 2; ++cb) {
+                    const int v = 32 * cb + (int)lane;
+                    if (cb < geo.nblk && v < st.nv)
+                        cpa16(rows_s + geo.off[cb] + (uint32_t)r * geo.stride[cb] + lane * 16u, src + (size_t)v * 16);
+                }
+            }
+            // worst-key snapshots
+            if ((int)lane < ns) cpa8(su32(swk + lane), st.keys + (size_t)id0 * K + (K - 1));
+            if ((int)lane + 32 < ns) cpa8(su32(swk + lane + 32), st.keys + (size_t)id1 * K + (K - 1));
+            __syncwarp();
+            bar_arrive_copies(&sh->full[slot]);
+            if (lane == 0) bar_arrive(&sh->full[slot]);
+            ++k;
+            u = next_node(u + gridDim.x, meta, id0, id1);
+        }
+        if (!ok && lane == 0 && !*abort_flag) {
+            sh->abort_flag = 1;
+            ++w_to;
+        }
+        // every copy issued lands before the block can exit
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else {
+        // ---------------------------------------------------------- compute --
+        long long l_evals = 0, l_gath = 0, l_props = 0, l_ovf = 0, l_ins = 0;
+        for (int k = 0;; ++k) {
+            const int slot = k & 1;
+            const unsigned char *sb = slots + (size_t)slot * geo.slot_bytes;
+            if (!bar_wait(&sh->full[slot], (k >> 1) & 1, abort_flag)) {
+                if (tid == 0 && !*abort_flag) {
+                    sh->abort_flag = 1;
+                    ++w_to;
+                }
+                break;
+            }
+            const int *hdr = reinterpret_cast<const int *>(sb);
+            const int ns = hdr[0], m = hdr[1], o = ns - m;
+            if (ns == 0) break;
+            const int *ssid = hdr + 4;
+            const uint64_t *sswk = reinterpret_cast<const uint64_t *>(sb + 16 + 4 * kSetMax);
+            if (tid < ns) {
+                cur->sid[tid] = ssid[tid];
+                cur->swk[tid] = sswk[tid];
+                cur->mask[tid] = 0ull;
+                cur->fails[tid] = 0ull;
+            }
+            if (tid < 2) cur->failed[tid] = 0u;
+            // ---- 1. distance block (RB so that the items fill the block)
+            const unsigned char *rows = sb + kPipeHdrBytes;
+            const int nb = (ns + 3) >> 2;
+            if (((m + 1) >> 1) * nb >= kPipeCompute / 2) pipe_dist<2>(rows, geo, cur->D, ns, m, tid);
+            else pipe_dist<1>(rows, geo, cur->D, ns, m, tid);
+            compute_sync();
+            if (tid == 0) bar_arrive(&sh->empty[slot]);  // the rows are no longer read
+            if (tid == 0) {
+                l_evals += (long long)m * (m - 1) / 2 + (long long)m * o;
+                l_gath += ns;
+            }
+            // ---- 2. proposals that order before the target's worst entry
+            {
+                unsigned *mw = reinterpret_cast<unsigned *>(cur->mask);
+                const uint32_t nsm = div_magic((uint32_t)ns);
+                for (int e = tid; e < m * ns; e += kPipeCompute) {
+                    const int i = (int)div_small((uint32_t)e, (uint32_t)ns, nsm), j = e - i * ns;
+                    if (j == i) continue;
+                    const float dd = cur->D[i * kPipeDStride + j];
+                    if (make_key(dd, (uint32_t)cur->sid[j], kFlagNew | kFlagIns) < cur->swk[i])
+                        atomicOr(&mw[2 * i + (j >> 5)], 1u << (j & 31));
+                    if (j >= m && make_key(dd, (uint32_t)cur->sid[i], kFlagNew | kFlagIns) < cur->swk[j])
+                        atomicOr(&mw[2 * j + (i >> 5)], 1u << (i & 31));
+                }
+            }
+            compute_sync();
+            // ---- 3a. reservation: warp 0, targets lane and 32 + lane
+            if (warp == 0) {
+                const unsigned long long ma = (int)lane < ns ? cur->mask[lane] : 0ull;
+                const unsigned long long mb = (int)lane + 32 < ns ? cur->mask[lane + 32] : 0ull;
+                const int ca = __popcll(ma), cbn = __popcll(mb);
+                int ba = 0, bb = 0;
+                if (ca) ba = atomicAdd(st.pcursor + cur->sid[lane], ca);
+                if (cbn) bb = atomicAdd(st.pcursor + cur->sid[lane + 32], cbn);
+                if (ca)
+                    for (int r = ba >> kBucketRunBits > 1 ? ba >> kBucketRunBits : 1; r <= (ba + ca - 1) >> kBucketRunBits;
+                         ++r)
+                        bucket_slot(st, (uint32_t)cur->sid[lane], r << kBucketRunBits);
+                if (cbn)
+                    for (int r = bb >> kBucketRunBits > 1 ? bb >> kBucketRunBits : 1;
+                         r <= (bb + cbn - 1) >> kBucketRunBits; ++r)
+                        bucket_slot(st, (uint32_t)cur->sid[lane + 32], r << kBucketRunBits);
+                int inc0 = ca, inc1 = cbn;
+                for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                    const int v = __shfl_up_sync(kFull, inc0, o2);
+                    if ((int)lane >= o2) inc0 += v;
+                }
+                const int tot0 = __shfl_sync(kFull, inc0, 31);
+                for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                    const int v = __shfl_up_sync(kFull, inc1, o2);
+                    if ((int)lane >= o2) inc1 += v;
+                }
+                inc1 += tot0;
+                // targets past ns have no proposals: their prefix is the total
+                cur->incl[lane] = inc0;
+                cur->incl[lane + 32] = inc1;
+                if ((int)lane < ns) cur->rbase[lane] = ba - (inc0 - ca);
+                if ((int)lane + 32 < ns) cur->rbase[lane + 32] = bb - (inc1 - cbn);
+                if (lane == 31) cur->total = inc1;
+                l_props += ca + cbn;
+            }
+            compute_sync();
+            // ---- 3b. proposals flattened over the block
+            const int total = cur->total;
+            for (int kk = tid; kk < total; kk += kPipeCompute) {
+                // target: the number of targets whose inclusive prefix is <= kk
+                int t = 0;
+#pragma unroll
+                for (int step = 32; step > 0; step >>= 1)
+                    if (cur->incl[t + step - 1] <= kk) t += step;
+                const int excl = t == 0 ? 0 : cur->incl[t - 1];
+                const int j = nth_set_bit64(cur->mask[t], kk - excl);
+                uint64_t *dst = bucket_slot(st, (uint32_t)cur->sid[t], kk + cur->rbase[t]);
+                const float dd = t < m ? cur->D[t * kPipeDStride + j] : cur->D[j * kPipeDStride + t];
+                if (dst) {
+                    *dst = make_key(dd, (uint32_t)cur->sid[j], kFlagNew | kFlagIns);
+                } else {
+                    atomicOr(&cur->fails[t], 1ull << j);
+                    atomicOr(&cur->failed[t >> 5], 1u << (t & 31));
+                }
+            }
+            compute_sync();
+            // ---- full buckets (rare): locked insertion, one warp per target
+            const unsigned long long fm = (unsigned long long)cur->failed[0] | ((unsigned long long)cur->failed[1] << 32);
+            if (fm) {
+                int idx = 0;
+                for (unsigned long long mm = fm; mm; mm &= mm - 1, ++idx) {
+                    if (idx % kPipeWarps != warp) continue;
+                    const int t = __ffsll((long long)mm) - 1;
+                    const unsigned long long rest = cur->fails[t];
+                    if (lane == 0) l_ovf += __popcll(rest);
+                    uint64_t xs[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = (int)lane + 32 * h;
+                        xs[h] = kKeyEmpty;
+                        if ((rest >> j) & 1ull) {
+                            const float dd = t < m ? cur->D[t * kPipeDStride + j] : cur->D[j * kPipeDStride + t];
+                            xs[h] = make_key(dd, (uint32_t)cur->sid[j], kFlagNew | kFlagIns);
+                        }
+                    }
+                    const int ins = warp_locked_insert(st, (uint32_t)cur->sid[t], rest, xs[0], xs[1]);
+                    if (lane == 0) {
+                        if (ins < 0) ++w_to;
+                        else l_ins += ins;
+                    }
+                }
+            }
+            compute_sync();  // cur is reused by the next node
+        }
+        const long long w_props = warp_sum(l_props);
+        if (lane == 0 && w_props) atomic_add_ll(&sh->stat[2], w_props);
+        if (tid == 0) {
+            atomic_add_ll(&sh->stat[0], l_evals);
+            atomic_add_ll(&sh->stat[1], l_gath);
+        }
+        if (l_ins) atomic_add_ll(&sh->stat[3], l_ins);
+        if (l_ovf) atomic_add_ll(&sh->stat[4], l_ovf);
+    }
+    if (w_to) atomic_add_ll(&sh->stat[5], w_to);
+    __syncthreads();
+    if (tid == 0) {
+        long long *its = st.it_stats + (size_t)li * kItCount;
+        its[kItRan] = 1;
+        atomic_add_ll(&its[kItEvals], sh->stat[0]);
+        atomic_add_ll(&its[kItGathered], sh->stat[1]);
+        atomic_add_ll(&its[kItProposals], sh->stat[2]);
+        atomic_add_ll(&its[kItInserts], sh->stat[3]);
+        atomic_add_ll(&st.stats[kStatEvals], sh->stat[0]);
+        atomic_add_ll(&st.stats[kStatGathered], sh->stat[1]);
+        atomic_add_ll(&st.stats[kStatInserts], sh->stat[3]);
+        if (sh->stat[4]) atomic_add_ll(&st.stats[kStatBucketOverflow], sh->stat[4]);
+        if (sh->stat[5]) atomic_add_ll(&st.stats[kStatLockTimeout], sh->stat[5]);
+    }
+}
+
+bool pipe_join_fits(int bf16, int nv) { return !bf16 && nv > 8 && nv <= kPipeMaxUnits; }
+
+cudaError_t launch_pipe_join(const DevState &st, int li, cudaStream_t s) {
+    cudaError_t e = launch_set_kernel(st, li, s);
+    if (e != cudaSuccess) return e;
+    const size_t dyn = pipe_smem_bytes(st.nv);
+    e = smem_opt_in((const void *)pipe_join_kernel, dyn);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_for((const void *)pipe_join_kernel, kPipeThreads, dyn);
+    pipe_join_kernel<<<grid, kPipeThreads, dyn, s>>>(st, li);
+    return cudaGetLastError();
+}
+
+}  // namespace knng

@@ -784,11 +784,15 @@ cudaError_t launch_ring_t(const DevState &st, int li, cudaStream_t s) {
 }
 }  // namespace
 
-cudaError_t launch_ring_join(const DevState &st, int li, cudaStream_t s) {
+cudaError_t launch_set_kernel(const DevState &st, int li, cudaStream_t s) {
     const size_t dyn = set_kernel_smem(st.cap);
     const int grid = grid_for((const void *)set_kernel, kSetWarps * 32, dyn);
     set_kernel<<<grid, kSetWarps * 32, dyn, s>>>(st, li);
-    cudaError_t e = cudaGetLastError();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ring_join(const DevState &st, int li, cudaStream_t s) {
+    cudaError_t e = launch_set_kernel(st, li, s);
     if (e != cudaSuccess) return e;
     return st.bf16 ? launch_ring_t<true>(st, li, s) : launch_ring_t<false>(st, li, s);
 }

@@ -195,16 +195,27 @@ PATH_CASES = [
     (1200, 64, 16, 0.5, 4, True),     # one 64-bf16 k-block
     (600, 128, 32, 0.3, 4, True),
     (2000, 150, 20, 1.0, 4, True),    # up to 64 candidates: four 16-row tiles
+    (2000, 200, 20, 1.0, 3, False),   # two column blocks of the pipelined kernel, up to 64 candidates
+    (1500, 33, 16, 0.5, 4, False),    # 9 float4 per row: the narrowest pipelined row
+    (3000, 256, 24, 0.5, 3, False),   # the widest pipelined row (64 float4)
 ]
-PATH_IDS = {"warp": 0, "tile": 1, "ring": 2}
+PATH_IDS = {"warp": 0, "tile": 1, "ring": 2, "pipe": 3}
 
 
-@pytest.mark.parametrize("path", ["tile", "ring"])
+def _pipe_eligible(d, bf16):
+    """The pipelined block kernel takes float32 rows of 33 to 256 floats."""
+    dp = (d + 3) // 4 * 4
+    return not bf16 and 32 < dp <= 256
+
+
+@pytest.mark.parametrize("path", ["tile", "ring", "pipe"])
 @pytest.mark.parametrize("n,d,K,rho,hi,bf16", PATH_CASES)
 def test_join_kernels_match_oracle_bit_exact(path, n, d, K, rho, hi, bf16, monkeypatch):
-    """The block-per-node tile kernel and the TMA-staged ring kernel, forced
-    on the same inputs: one iteration bit-exact against the oracle (integer
-    data: the bf16 expansion is exact too)."""
+    """The block-per-node tile kernel, the ring kernel and the pipelined
+    block kernel, forced on the same inputs: one iteration bit-exact against
+    the oracle (integer data: the bf16 expansion is exact too)."""
+    if path == "pipe" and not _pipe_eligible(d, bf16):
+        pytest.skip("rows outside the pipelined kernel's range")
     monkeypatch.setenv("KNNG_TEST_JOIN_PATH", path)
     x = _int_data(n, d, hi, seed=n + d)
     ids0, new0 = workloads.random_graph(n, K, seed=n + 1, p_new=0.6)
@@ -224,10 +235,10 @@ def test_join_kernels_match_oracle_bit_exact(path, n, d, K, rho, hi, bf16, monke
     assert stats["dist_evals"] == r["evals"]
 
 
-@pytest.mark.parametrize("path", ["warp", "tile", "ring"])
+@pytest.mark.parametrize("path", ["warp", "tile", "ring", "pipe"])
 def test_join_kernels_agree_on_real_valued_builds(path, monkeypatch):
     """Whole float32 builds on real-valued clustered data through each join
-    kernel: every float32 distance uses the same arithmetic, so the three
+    kernel: every float32 distance uses the same arithmetic, so the four
     kernels give the same graph bit for bit."""
     monkeypatch.setenv("KNNG_TEST_JOIN_PATH", path)
     x = workloads.gaussian_mixture(6000, 72, 20, seed=4)
@@ -260,9 +271,10 @@ def test_bucket_overflow_paths_match_oracle_bit_exact(pool, monkeypatch):
     assert ch == r["changes"]
 
 
-@pytest.mark.parametrize("path", ["tile", "ring"])
+@pytest.mark.parametrize("path", ["tile", "ring", "pipe"])
 def test_bucket_overflow_paths_high_d_kernels(path, monkeypatch):
-    """The same tiny-pool overflow drive through the tile and ring kernels."""
+    """The same tiny-pool overflow drive through the tile, ring and
+    pipelined kernels."""
     monkeypatch.setenv("KNNG_TEST_BUCKET_POOL_CHUNKS", "1")
     monkeypatch.setenv("KNNG_TEST_JOIN_PATH", path)
     n, d, K, rho, hi = 1800, 70, 16, 0.5, 3
@@ -489,7 +501,7 @@ def test_autotuned_builds_equal_default_builds():
     b_i, b_d, sb = knng.knng_build(_cuda(x), 16, 0.5, 0.001, 8, seed=4, flags=knng.FLAG_AUTOTUNE)
     assert torch.equal(a_i, ref_i) and torch.equal(a_d, ref_d)
     assert torch.equal(b_i, ref_i) and torch.equal(b_d, ref_d)
-    assert sa["join_path"] in (0, 1, 2) and sb["join_path"] == sa["join_path"]
+    assert sa["join_path"] in (0, 1, 2, 3) and sb["join_path"] == sa["join_path"]
     # the tuning build ran three trial joins on top of the real ones
     assert sa["kernel_launches"] > sb["kernel_launches"]
 
