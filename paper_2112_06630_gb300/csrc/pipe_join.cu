@@ -22,15 +22,17 @@
 //        columns per thread, RB chosen per node (2 or 1) so that small
 //        nodes still spread over the block; then the row slot is released
 //        to the producer;
-//     2. proposal masks: element (i, j) carries j to i (j != i) and, for an
-//        old j, i to j -- every proposal of the node's join pairs once -- kept
-//        when its key orders before the target's snapshot worst entry;
-//     3. bucket runs: one lane per target reserves the target's range (one
-//        atomicAdd) and claims the pool chunks it spans; every thread then
-//        writes proposals flattened over the block (target by a binary search
-//        over the per-target prefix counts, partner as the r-th set bit of
-//        the target's mask); a proposal whose run has no slot (bucket or pool
-//        spent) is inserted into the list under the list's lock.
+//     2. proposals, one warp per target: a new target takes partner j when
+//        key(D[t][j], j) orders before its snapshot worst entry, an old target
+//        takes new partner i when key(D[i][t], i) does -- every proposal of the
+//        node's join pairs once -- two ballots giving the target's mask;
+//     3. bucket runs: the lanes of a warp reserve its targets' ranges at once
+//        (one atomicAdd each) and claim the pool chunks they span, then write
+//        the warp's proposals flattened over its lanes (target by a search
+//        over the lanes' prefix counts, partner as the r-th set bit of its
+//        mask); a proposal whose run has no slot (bucket or pool spent) is
+//        inserted into the list under the list's lock.
+// Two block barriers per node: after the distance block, and at its end.
 // The proposals are those of the other join kernels, so the lists after the
 // merge are the same bit for bit.  Every wait is bounded by the global timer;
 // a wait that gives up raises the timeout counter and the block winds down
@@ -81,12 +83,7 @@ __host__ __device__ __forceinline__ PipeGeo pipe_geo(int nv) {
 struct PipeCur {
     int sid[kSetMax];
     uint64_t swk[kSetMax];
-    unsigned long long mask[kSetMax];
-    unsigned long long fails[kSetMax];
-    int incl[kSetMax];          // inclusive prefix counts of proposals per target
-    int rbase[kSetMax];         // reserved start minus exclusive prefix
-    unsigned failed[2];         // targets with a proposal that found no slot
-    int total;
+    unsigned long long fails[kSetMax];  // per target: proposals that found no bucket slot
     float D[kSetMax * kPipeDStride];
 };
 
@@ -330,10 +327,8 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
             if (tid < ns) {
                 cur->sid[tid] = ssid[tid];
                 cur->swk[tid] = sswk[tid];
-                cur->mask[tid] = 0ull;
                 cur->fails[tid] = 0ull;
             }
-            if (tid < 2) cur->failed[tid] = 0u;
             // ---- 1. distance block (RB so that the items fill the block)
             const unsigned char *rows = sb + kPipeHdrBytes;
             const int nb = (ns + 3) >> 2;
@@ -345,84 +340,100 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
                 l_evals += (long long)m * (m - 1) / 2 + (long long)m * o;
                 l_gath += ns;
             }
-            // ---- 2. proposals that order before the target's worst entry
-            {
-                unsigned *mw = reinterpret_cast<unsigned *>(cur->mask);
-                const uint32_t nsm = div_magic((uint32_t)ns);
-                for (int e = tid; e < m * ns; e += kPipeCompute) {
-                    const int i = (int)div_small((uint32_t)e, (uint32_t)ns, nsm), j = e - i * ns;
-                    if (j == i) continue;
-                    const float dd = cur->D[i * kPipeDStride + j];
-                    if (make_key(dd, (uint32_t)cur->sid[j], kFlagNew | kFlagIns) < cur->swk[i])
-                        atomicOr(&mw[2 * i + (j >> 5)], 1u << (j & 31));
-                    if (j >= m && make_key(dd, (uint32_t)cur->sid[i], kFlagNew | kFlagIns) < cur->swk[j])
-                        atomicOr(&mw[2 * j + (i >> 5)], 1u << (i & 31));
-                }
-            }
-            compute_sync();
-            // ---- 3a. reservation: warp 0, targets lane and 32 + lane
-            if (warp == 0) {
-                const unsigned long long ma = (int)lane < ns ? cur->mask[lane] : 0ull;
-                const unsigned long long mb = (int)lane + 32 < ns ? cur->mask[lane + 32] : 0ull;
-                const int ca = __popcll(ma), cbn = __popcll(mb);
-                int ba = 0, bb = 0;
-                if (ca) ba = atomicAdd(st.pcursor + cur->sid[lane], ca);
-                if (cbn) bb = atomicAdd(st.pcursor + cur->sid[lane + 32], cbn);
-                if (ca)
-                    for (int r = ba >> kBucketRunBits > 1 ? ba >> kBucketRunBits : 1; r <= (ba + ca - 1) >> kBucketRunBits;
-                         ++r)
-                        bucket_slot(st, (uint32_t)cur->sid[lane], r << kBucketRunBits);
-                if (cbn)
-                    for (int r = bb >> kBucketRunBits > 1 ? bb >> kBucketRunBits : 1;
-                         r <= (bb + cbn - 1) >> kBucketRunBits; ++r)
-                        bucket_slot(st, (uint32_t)cur->sid[lane + 32], r << kBucketRunBits);
-                int inc0 = ca, inc1 = cbn;
-                for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                    const int v = __shfl_up_sync(kFull, inc0, o2);
-                    if ((int)lane >= o2) inc0 += v;
-                }
-                const int tot0 = __shfl_sync(kFull, inc0, 31);
-                for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                    const int v = __shfl_up_sync(kFull, inc1, o2);
-                    if ((int)lane >= o2) inc1 += v;
-                }
-                inc1 += tot0;
-                // targets past ns have no proposals: their prefix is the total
-                cur->incl[lane] = inc0;
-                cur->incl[lane + 32] = inc1;
-                if ((int)lane < ns) cur->rbase[lane] = ba - (inc0 - ca);
-                if ((int)lane + 32 < ns) cur->rbase[lane + 32] = bb - (inc1 - cbn);
-                if (lane == 31) cur->total = inc1;
-                l_props += ca + cbn;
-            }
-            compute_sync();
-            // ---- 3b. proposals flattened over the block
-            const int total = cur->total;
-            for (int kk = tid; kk < total; kk += kPipeCompute) {
-                // target: the number of targets whose inclusive prefix is <= kk
-                int t = 0;
-#pragma unroll
-                for (int step = 32; step > 0; step >>= 1)
-                    if (cur->incl[t + step - 1] <= kk) t += step;
-                const int excl = t == 0 ? 0 : cur->incl[t - 1];
-                const int j = nth_set_bit64(cur->mask[t], kk - excl);
-                uint64_t *dst = bucket_slot(st, (uint32_t)cur->sid[t], kk + cur->rbase[t]);
-                const float dd = t < m ? cur->D[t * kPipeDStride + j] : cur->D[j * kPipeDStride + t];
-                if (dst) {
-                    *dst = make_key(dd, (uint32_t)cur->sid[j], kFlagNew | kFlagIns);
+            // ---- 2. proposals, one warp per target (targets warp, warp + 8,
+            //         ...): a new target t takes partner j (j != t) when
+            //         key(D[t][j], j) orders before t's snapshot worst, an old
+            //         target t takes new partner i when key(D[i][t], i) does --
+            //         every proposal of the node's join pairs once.  Two
+            //         ballots give a target's 64-bit mask; lane q keeps the
+            //         mask of the warp's target q.
+            const int nt = warp < ns ? (ns - warp + kPipeWarps - 1) / kPipeWarps : 0;
+            unsigned long long my_mask = 0ull;
+            for (int q = 0; q < nt; ++q) {
+                const int t = warp + kPipeWarps * q;
+                const uint64_t wt = cur->swk[t];
+                unsigned b0, b1;
+                if (t < m) {
+                    const int j0 = (int)lane, j1 = (int)lane + 32;
+                    b0 = __ballot_sync(kFull, j0 < ns && j0 != t &&
+                                                  make_key(cur->D[t * kPipeDStride + j0], (uint32_t)cur->sid[j0],
+                                                           kFlagNew | kFlagIns) < wt);
+                    b1 = __ballot_sync(kFull, j1 < ns && j1 != t &&
+                                                  make_key(cur->D[t * kPipeDStride + j1], (uint32_t)cur->sid[j1],
+                                                           kFlagNew | kFlagIns) < wt);
                 } else {
-                    atomicOr(&cur->fails[t], 1ull << j);
-                    atomicOr(&cur->failed[t >> 5], 1u << (t & 31));
+                    const int i0 = (int)lane, i1 = (int)lane + 32;
+                    b0 = __ballot_sync(kFull, i0 < m &&
+                                                  make_key(cur->D[i0 * kPipeDStride + t], (uint32_t)cur->sid[i0],
+                                                           kFlagNew | kFlagIns) < wt);
+                    b1 = __ballot_sync(kFull, i1 < m &&
+                                                  make_key(cur->D[i1 * kPipeDStride + t], (uint32_t)cur->sid[i1],
+                                                           kFlagNew | kFlagIns) < wt);
                 }
+                if ((int)lane == q) my_mask = (unsigned long long)b0 | ((unsigned long long)b1 << 32);
             }
-            compute_sync();
-            // ---- full buckets (rare): locked insertion, one warp per target
-            const unsigned long long fm = (unsigned long long)cur->failed[0] | ((unsigned long long)cur->failed[1] << 32);
-            if (fm) {
-                int idx = 0;
-                for (unsigned long long mm = fm; mm; mm &= mm - 1, ++idx) {
-                    if (idx % kPipeWarps != warp) continue;
-                    const int t = __ffsll((long long)mm) - 1;
+            // ---- 3. bucket runs of the warp's targets: lanes q < nt reserve
+            //         their target's range at once (one atomicAdd each) and
+            //         claim the pool chunks it spans; then lane k writes
+            //         proposal k of the warp's targets (target by a search over
+            //         the lanes' prefix counts, partner as the r-th set bit)
+            {
+                const int cnt = (int)lane < nt ? __popcll(my_mask) : 0;
+                const int t_me = warp + kPipeWarps * (int)lane;
+                int base = 0;
+                if (cnt) {
+                    const uint32_t p = (uint32_t)cur->sid[t_me];
+                    base = atomicAdd(st.pcursor + p, cnt);
+                    for (int r = base >> kBucketRunBits > 1 ? base >> kBucketRunBits : 1;
+                         r <= (base + cnt - 1) >> kBucketRunBits; ++r)
+                        bucket_slot(st, p, r << kBucketRunBits);
+                }
+                int inc = cnt;
+#pragma unroll
+                for (int o2 = 1; o2 < 8; o2 <<= 1) {
+                    const int v = __shfl_up_sync(kFull, inc, o2);
+                    if ((int)lane >= o2) inc += v;
+                }
+                const int total_w = __shfl_sync(kFull, inc, 7);
+                const int rb = base - (inc - cnt);
+                l_props += (lane == 0) ? total_w : 0;
+                __threadfence_block();
+                unsigned fail_q = 0;  // lane q: the target q had a proposal without a slot
+                for (int k0 = 0; k0 < total_w; k0 += 32) {
+                    const int kk = k0 + (int)lane;
+                    const bool act = kk < total_w;
+                    const int kc = act ? kk : total_w - 1;
+                    int q = 0;
+#pragma unroll
+                    for (int step = 4; step > 0; step >>= 1) {
+                        const int v = __shfl_sync(kFull, inc, q + step - 1);
+                        if (v <= kc) q += step;
+                    }
+                    const int qe = q > 0 ? q - 1 : 0;
+                    const int ev = __shfl_sync(kFull, inc, qe);
+                    const unsigned long long mq = __shfl_sync(kFull, my_mask, q);
+                    const int rbq = __shfl_sync(kFull, rb, q);
+                    const int excl = q == 0 ? 0 : ev;
+                    unsigned failed_here = 0;
+                    if (act) {
+                        const int t = warp + kPipeWarps * q;
+                        const int j = nth_set_bit64(mq, kk - excl);
+                        uint64_t *dst = bucket_slot(st, (uint32_t)cur->sid[t], kk + rbq);
+                        const float dd = t < m ? cur->D[t * kPipeDStride + j] : cur->D[j * kPipeDStride + t];
+                        if (dst) {
+                            *dst = make_key(dd, (uint32_t)cur->sid[j], kFlagNew | kFlagIns);
+                        } else {
+                            atomicOr(&cur->fails[t], 1ull << j);
+                            failed_here = 1u << q;
+                        }
+                    }
+                    fail_q |= __reduce_or_sync(kFull, failed_here);
+                }
+                __syncwarp();
+                // full buckets (rare): this warp's targets, locked insertion
+                for (unsigned fm = fail_q; fm; fm &= fm - 1) {
+                    const int q = __ffs(fm) - 1;
+                    const int t = warp + kPipeWarps * q;
                     const unsigned long long rest = cur->fails[t];
                     if (lane == 0) l_ovf += __popcll(rest);
                     uint64_t xs[2];
