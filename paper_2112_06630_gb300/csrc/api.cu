@@ -197,6 +197,8 @@ struct knng_ctx {
         st.cset = cset;
         st.cmeta = cmeta;
         st.join_path = join_path;
+        st.u_lo = 0;
+        st.u_hi = n;
         return st;
     }
 };
@@ -503,6 +505,22 @@ int autotune_join(knng_ctx *c, int li) {
     return KNNG_OK;
 }
 
+// Node-range passes of iteration `it`'s join.  Proposal capacity per pass:
+// one 256-key run per node plus the pool.  A node joins up to m = min(64, 2s)
+// new candidates (s forward and about s reverse), whose pairs give up to
+// m (m - 1) proposals; in the first iteration the lists are random and nearly
+// all of them pass the worst-key filter, later ones about 70% at most
+// (measured on the 1M x 128 mixture at s = 23).  Most workloads take one pass.
+int join_passes(const knng_ctx *c, int it) {
+    // test hook: a fixed number of passes (parity of the pass split)
+    if (const char *e = std::getenv("KNNG_TEST_JOIN_PASSES")) return std::max(1, std::min(std::atoi(e), 64));
+    const double m = std::min(kSetMax, 2 * c->s);
+    const double want = (double)c->n * m * (m - 1.0) * (it <= 1 ? 1.0 : 0.7);
+    const double cap = 0.85 * ((double)c->n + (double)c->pool_chunks) * kBucketRun;
+    const int p = (int)std::ceil(want / cap);
+    return std::max(1, std::min(p, 16));
+}
+
 int enqueue_iteration(knng_ctx *c, bool gate) {
     if (c->li >= kMaxLocalIters) return KNNG_ERR_STATE;
     const int li = c->li, it = c->it_done + 1;
@@ -525,11 +543,21 @@ int enqueue_iteration(knng_ctx *c, bool gate) {
         st = c->dev(gate);
     }
     if (timing) KNNG_TRY(cudaEventRecord(ev[2], c->stream));
-    KNNG_TRY(launch_join(st, li, c->stream));
-    if (timing) KNNG_TRY(cudaEventRecord(ev[3], c->stream));
-    KNNG_TRY(launch_merge(st, li, c->stream));
+    // the join in node-range passes, each followed by a list merge, so that
+    // one pass's proposals fit the buckets and the pool (the set kernel runs
+    // with the first pass; later passes filter against the merged lists)
+    const int passes = join_passes(c, it);
+    for (int p = 0; p < passes; ++p) {
+        st.u_lo = c->n * p / passes;
+        st.u_hi = c->n * (p + 1) / passes;
+        KNNG_TRY(launch_join(st, li, c->stream));
+        if (p + 1 == passes && timing) KNNG_TRY(cudaEventRecord(ev[3], c->stream));
+        KNNG_TRY(launch_merge(st, li, c->stream));
+        if (p + 1 < passes) KNNG_TRY(cudaMemsetAsync(c->pool_next, 0, sizeof(int), c->stream));
+    }
     if (timing) KNNG_TRY(cudaEventRecord(ev[4], c->stream));
-    c->launches += (c->heap ? 5 : 3) + join_launches(c->join_path);
+    c->launches += (c->heap ? 4 : 2) + passes * (1 + join_launches(c->join_path)) - (passes - 1) *
+                   (join_launches(c->join_path) - 1);
     c->li++;
     c->it_done++;
     if ((c->flags & KNNG_FLAG_REORDER) && !c->reordered && it == 1) {

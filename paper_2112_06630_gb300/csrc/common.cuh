@@ -221,6 +221,10 @@ struct DevState {
     int *cset;                 // n x 64 candidate ids, new ones first
     int *cmeta;                // n: ns | m << 8 (0: no join pair)
     int join_path;             // JoinPath chosen for this context
+    // nodes whose joins this launch runs, [u_lo, u_hi): the whole set, or one
+    // pass of an iteration split into node ranges with a list merge after
+    // each (the set kernel runs once, with the first pass)
+    long long u_lo, u_hi;
 };
 
 // Which local-join kernel a context uses (fixed at creation).

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
 
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long u = gw; u < st.n; u += nw) {
+    for (long long u = st.u_lo + gw; u < st.u_hi; u += nw) {
         if (node_skipped(st, u, li)) continue;  // batched: u's data set converged
         // ---- 1. candidates of u, repeats removed (new first, then old)
         int ns, m;
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
                     xs[h] = make_key(l2sq_rows(rt, rj, nv), (uint32_t)sid[j], kFlagNew | kFlagIns);
                 }
             }
-            const int ins = warp_locked_insert(st, p, rest, xs[0], xs[1]);
+            const int ins = warp_locked_insert(st, p, rest, xs[0], xs[1], li);
             if (ins < 0) ++w_to;
             else w_ins += ins;
         }
@@ -451,6 +451,9 @@ __global__ void __launch_bounds__(kMergeWarps * 32, 4) merge_kernel(DevState st,
         uint64_t *row = st.keys + (size_t)p * K;
         int *chunks = st.pchunk + (size_t)p * kBucketChunks;
         uint64_t Lk = valid ? row[lane] : kKeyEmpty;
+        // entries already inserted in this iteration (an earlier pass's merge
+        // or a locked insertion, which counted them)
+        const int ch0 = __popc(__ballot_sync(kFull, valid && (Lk & kFlagIns)));
         int ins = 0;
         const bool bf16 = st.bf16 != 0;
         // the inline run, its loads two batches ahead of the merges
@@ -480,8 +483,9 @@ __global__ void __launch_bounds__(kMergeWarps * 32, 4) merge_kernel(DevState st,
             ins += merge_batch(Lk, x, K, bf16, scratch);
         }
         // entries flagged "inserted in this iteration" that are still listed
-        // (the sampling pass cleared that flag everywhere before the join)
-        const int ch = __popc(__ballot_sync(kFull, valid && (Lk & kFlagIns)));
+        // (the sampling pass cleared that flag everywhere before the join),
+        // less those already counted
+        const int ch = __popc(__ballot_sync(kFull, valid && (Lk & kFlagIns))) - ch0;
         w_changes += ch;
         if (st.ds) {
             const int b = st.ds[p];

@@ -132,9 +132,13 @@ __device__ __forceinline__ int warp_gather_candidates(const DevState &st, long l
 // Locked insertion (one warp) of proposals into node p's list, used when a
 // proposal bucket is full.  Lane j holds the key of partner j in x0 and of
 // partner 32 + j in x1; `rest` selects the partners.  The lock wait is
-// bounded; returns -1 when it gave up, else the number of insertions.
+// bounded; returns -1 when it gave up, else the number of insertions.  The
+// list's entries inserted in this iteration (flag kFlagIns) before and after
+// are counted, and the difference is added to iteration li's change count
+// (and to its data set's in batched mode): list merges add theirs the same
+// way, so the count is exact however the updates of a list interleave.
 __device__ __forceinline__ int warp_locked_insert(const DevState &st, uint32_t p, unsigned long long rest,
-                                                  uint64_t x0, uint64_t x1) {
+                                                  uint64_t x0, uint64_t x1, int li) {
     const unsigned lane = lane_id();
     const int K = st.K;
     bool got = false;
@@ -152,11 +156,17 @@ __device__ __forceinline__ int warp_locked_insert(const DevState &st, uint32_t p
     if (!got) return -1;
     uint64_t *row = st.keys + (size_t)p * K;
     uint64_t Lk = (int)lane < K ? __ldcg(row + lane) : kKeyEmpty;
+    const int before = __popc(__ballot_sync(kFull, (int)lane < K && (Lk & kFlagIns)));
     int ins = 0;
     for (unsigned long long mm = rest; mm; mm &= mm - 1) {
         const int j = __ffsll((long long)mm) - 1;
         const uint64_t xa = __shfl_sync(kFull, x0, j & 31), xb = __shfl_sync(kFull, x1, j & 31);
         ins += warp_insert(Lk, j < 32 ? xa : xb, K);
+    }
+    const int after = __popc(__ballot_sync(kFull, (int)lane < K && (Lk & kFlagIns)));
+    if (lane == 0 && after != before) {
+        atomic_add_ll(st.it_stats + (size_t)li * kItCount + kItChanges, after - before);
+        if (st.ds) atomic_add_ll(st.ds_changes + (size_t)st.ds[p] * kMaxLocalIters + li, after - before);
     }
     if ((int)lane < K) __stcg(row + lane, Lk);
     __threadfence();

@@ -236,9 +236,9 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
         int k = 0;  // nodes handed out
         bool ok = true;
         // the next node of this block with a join pair (ids in registers)
-        long long u = blockIdx.x;
+        long long u = st.u_lo + blockIdx.x;
         auto next_node = [&](long long from, int &meta, int &id0, int &id1) -> long long {
-            for (long long v = from; v < st.n; v += gridDim.x) {
+            for (long long v = from; v < st.u_hi; v += gridDim.x) {
                 meta = __ldg(st.cmeta + v);
                 if (meta & 0xFF) {
                     const int ns = meta & 0xFF;
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
                     return v;
                 }
             }
-            return st.n;
+            return st.u_hi;
         };
         int meta = 0, id0 = 0, id1 = 0;
         u = next_node(u, meta, id0, id1);
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
             int *hdr = reinterpret_cast<int *>(sb);
             int *sid = hdr + 4;
             uint64_t *swk = reinterpret_cast<uint64_t *>(sb + 16 + 4 * kSetMax);
-            if (u >= st.n) {
+            if (u >= st.u_hi) {
                 // end mark: no rows; the copy arrivals complete at once
                 if (lane == 0) hdr[0] = 0;
                 __syncwarp();
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
                             xs[h] = make_key(dd, (uint32_t)cur->sid[j], kFlagNew | kFlagIns);
                         }
                     }
-                    const int ins = warp_locked_insert(st, (uint32_t)cur->sid[t], rest, xs[0], xs[1]);
+                    const int ins = warp_locked_insert(st, (uint32_t)cur->sid[t], rest, xs[0], xs[1], li);
                     if (lane == 0) {
                         if (ins < 0) ++w_to;
                         else l_ins += ins;
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
 bool pipe_join_fits(int bf16, int nv) { return !bf16 && nv > 8 && nv <= kPipeMaxUnits; }
 
 cudaError_t launch_pipe_join(const DevState &st, int li, cudaStream_t s) {
-    cudaError_t e = launch_set_kernel(st, li, s);
+    cudaError_t e = st.u_lo == 0 ? launch_set_kernel(st, li, s) : cudaSuccess;
     if (e != cudaSuccess) return e;
     const size_t dyn = pipe_smem_bytes(st.nv);
     e = smem_opt_in((const void *)pipe_join_kernel, dyn);

@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) ring_join_kernel(DevState st,
 
     if (warp == 0) {
         // ------------------------------------------------------ producer --
-        const long long ngroups = (st.n + kGroup - 1) / kGroup;
+        const long long ngroups = (st.u_hi - st.u_lo + kGroup - 1) / kGroup;
         int k_head = 0;  // nodes handed out
         ByteRing ra{0u, 0u, ring_a_cap, 0}, rb{0u, 0u, ring_b_cap, 0};
         bool ok = true;
@@ -420,12 +420,12 @@ __global__ void __launch_bounds__(kRingThreads, 1) ring_join_kernel(DevState st,
         auto load_group = [&](long long g) {
             nmeta = 0;
             if (g >= ngroups) return;
-            const long long u0 = g * kGroup;
-            if ((int)lane < kGroup && u0 + lane < st.n) nmeta = __ldg(st.cmeta + u0 + lane);
+            const long long u0 = st.u_lo + g * kGroup;
+            if ((int)lane < kGroup && u0 + lane < st.u_hi) nmeta = __ldg(st.cmeta + u0 + lane);
 #pragma unroll
             for (int j = 0; j < kGroup; ++j) {
                 nids[j][0] = nids[j][1] = 0;
-                if (u0 + j < st.n) {
+                if (u0 + j < st.u_hi) {
                     nids[j][0] = __ldg(st.cset + (size_t)(u0 + j) * kSetMax + lane);
                     nids[j][1] = __ldg(st.cset + (size_t)(u0 + j) * kSetMax + 32 + lane);
                 }
@@ -704,7 +704,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) ring_join_kernel(DevState st,
                         xs[h] = make_key(dd, (uint32_t)sid[j], kFlagNew | kFlagIns);
                     }
                 }
-                const int ins = warp_locked_insert(st, (uint32_t)sid[t], rest, xs[0], xs[1]);
+                const int ins = warp_locked_insert(st, (uint32_t)sid[t], rest, xs[0], xs[1], li);
                 if (ins < 0) ++w_to;
                 else w_ins += ins;
             }
@@ -792,7 +792,7 @@ cudaError_t launch_set_kernel(const DevState &st, int li, cudaStream_t s) {
 }
 
 cudaError_t launch_ring_join(const DevState &st, int li, cudaStream_t s) {
-    cudaError_t e = launch_set_kernel(st, li, s);
+    cudaError_t e = st.u_lo == 0 ? launch_set_kernel(st, li, s) : cudaSuccess;
     if (e != cudaSuccess) return e;
     return st.bf16 ? launch_ring_t<true>(st, li, s) : launch_ring_t<false>(st, li, s);
 }

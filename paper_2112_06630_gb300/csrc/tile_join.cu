@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_join_kernel(DevState st, in
     long long t_evals = 0, t_gathered = 0, t_candids = 0, t_setovf = 0, t_props = 0, t_ovf = 0, t_ins = 0,
               t_to = 0;
     __syncthreads();
-    for (long long u = blockIdx.x; u < st.n; u += gridDim.x) {
+    for (long long u = st.u_lo + blockIdx.x; u < st.u_hi; u += gridDim.x) {
         if (node_skipped(st, u, li)) continue;  // batched: u's data set converged (uniform in the block)
         // ---- 1. candidates (warp 0)
         if (warp == 0) {
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_join_kernel(DevState st, in
                             xs[h] = make_key(dd, (uint32_t)sm.sid[j], kFlagNew | kFlagIns);
                         }
                     }
-                    const int ins = warp_locked_insert(st, (uint32_t)sm.sid[t], rest, xs[0], xs[1]);
+                    const int ins = warp_locked_insert(st, (uint32_t)sm.sid[t], rest, xs[0], xs[1], li);
                     if (lane == 0) {
                         if (ins < 0) ++t_to;
                         else t_ins += ins;

@@ -3,8 +3,9 @@ runs out must come back as an error status that the host reads, and the
 library and the GPU must stay usable afterwards.
 
 A test hook (KNNG_TEST_HOLD_LOCKS=h) starts the locks of the first h lists
-held, and a one-run proposal pool (KNNG_TEST_BUCKET_POOL_CHUNKS=1) sends
-proposals past full buckets to the locked insertion; an insertion into a held
+held, and a one-run proposal pool (KNNG_TEST_BUCKET_POOL_CHUNKS=1), with the
+join in one pass (KNNG_TEST_JOIN_PASSES=1), sends proposals past full buckets
+to the locked insertion; an insertion into a held
 list spins a bounded number of times (about half a second), gives up, raises
 the timeout counter, and the call returns KNNG_ERR_TIMEOUT.  Nothing traps,
 faults or hangs.
@@ -38,6 +39,7 @@ def test_held_locks_time_out_and_the_library_recovers(monkeypatch):
     x, ids0, new0, K, rho = _case()
     xd = torch.from_numpy(x).cuda()
     monkeypatch.setenv("KNNG_TEST_BUCKET_POOL_CHUNKS", "1")
+    monkeypatch.setenv("KNNG_TEST_JOIN_PASSES", "1")
     monkeypatch.setenv("KNNG_TEST_HOLD_LOCKS", "4")
     with knng.Context(xd, K, rho=rho, seed=11, graph=(ids0, new0), iter=0) as c:
         with pytest.raises(knng.KnngError) as err:
@@ -63,6 +65,7 @@ def test_held_locks_time_out_and_the_library_recovers(monkeypatch):
 def test_timeout_reported_by_the_one_shot_build(monkeypatch):
     x, _, _, K, rho = _case()
     monkeypatch.setenv("KNNG_TEST_BUCKET_POOL_CHUNKS", "1")
+    monkeypatch.setenv("KNNG_TEST_JOIN_PASSES", "1")
     monkeypatch.setenv("KNNG_TEST_HOLD_LOCKS", "4")
     with pytest.raises(knng.KnngError) as err:
         knng.knng_build(torch.from_numpy(x).cuda(), K, rho, 0.001, 2, seed=3)

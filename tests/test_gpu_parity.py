@@ -715,3 +715,36 @@ def test_parallel_relabel_edges():
         if n == 400:
             assert len(np.unique(levels[-1])) == 2
             assert set(sg[: n // 2].tolist()) in (set(range(n // 2)), set(range(n // 2, n)))
+
+
+@pytest.mark.parametrize("path", ["warp", "tile", "ring", "pipe"])
+@pytest.mark.parametrize("passes,pool", [(3, None), (5, "1")])
+def test_join_in_node_range_passes_matches_oracle_bit_exact(path, passes, pool, monkeypatch):
+    """An iteration's join split into node-range passes, each followed by a
+    list merge (what large sample rates use so that one pass's proposals fit
+    the buckets): by reading 6 the lists end the same, and the change count --
+    merges and locked insertions each adding the entries they made new --
+    equals the oracle's batched count.  With a one-chunk pool the passes also
+    run through poisoned runs and locked insertions."""
+    monkeypatch.setenv("KNNG_TEST_JOIN_PATH", path)
+    monkeypatch.setenv("KNNG_TEST_JOIN_PASSES", str(passes))
+    if pool:
+        monkeypatch.setenv("KNNG_TEST_BUCKET_POOL_CHUNKS", pool)
+    n, d, K, rho, hi = 1800, 8 if path == "warp" else 70, 16, 0.5, 3
+    x = _int_data(n, d, hi, seed=n + d)
+    ids0, new0 = workloads.random_graph(n, K, seed=n + 1, p_new=0.6)
+    with knng.Context(_cuda(x), K, rho=rho, seed=11, graph=(ids0, new0), iter=0) as c:
+        conv, ch = c.iterate()
+        gi, gd, gf = c.state()
+        stats = c.stats()
+    assert stats["join_path"] == PATH_IDS[path]
+    assert stats["set_overflow"] == 0 and stats["lock_timeouts"] == 0
+    if pool:
+        assert stats["bucket_overflow"] > 0
+    st = oracle.State(x, K, rho, seed=11)
+    st.init_graph(ids0, new0, 0)
+    r = st.iterate()
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    assert ch == r["changes"]
+    assert stats["dist_evals"] == r["evals"]
