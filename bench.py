@@ -591,7 +591,8 @@ def _time_builds(knng, xd, op, flags, steps, warmup, flush, stream, ws=1, seed=0
     return sum(times) / len(times), out
 
 
-JOIN_KERNELS = {0: "join_kernel", 1: "tile_join_kernel", 2: "set_kernel+ring_join_kernel"}
+JOIN_KERNELS = {0: "join_kernel", 1: "tile_join_kernel", 2: "set_kernel+ring_join_kernel",
+                3: "set_kernel+pipe_join_kernel"}
 
 
 def run_gpu(args):

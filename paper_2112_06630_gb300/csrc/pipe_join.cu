@@ -5,17 +5,17 @@
 //
 // The set kernel (ring_join.cu) has written each node's candidate set
 // (repeats removed, new first, at most 64) to cset / cmeta.  Each block of
-// pipe_join_kernel (persistent; one or two per SM) walks the nodes
+// pipe_join_kernel (persistent; up to four per SM) walks the nodes
 // u = blockIdx.x, blockIdx.x + gridDim.x, ...:
 //   producer warp: for every node with a join pair it takes a free row slot
-//     (two per block), writes the ids into it and issues asynchronous copies
+//     (one per block: the other blocks of the SM cover the wait), writes the ids into it and issues asynchronous copies
 //     of the candidate rows (one 16-byte cp.async per lane, a whole 512-byte
 //     row per warp instruction, rows on an odd number of 16-byte units so
 //     that consecutive rows start on different banks) and of each
 //     candidate's worst-key snapshot; the copies arrive on the slot's
-//     mbarrier, so the next node's rows land while the current one is
-//     computed;
-//   compute warps (eight, together on the current node):
+//     mbarrier, so the next node's rows land while the current one's
+//     proposals go out;
+//   compute warps (four, together on the current node):
 //     1. the distance block D[i][j] of the new rows i against all rows j, in
 //        the canonical float32 difference form (bit-identical to every other
 //        float32 distance of the library), register-blocked RB rows x 4
@@ -38,16 +38,25 @@
 // a wait that gives up raises the timeout counter and the block winds down
 // once the copies it issued have landed (again a bounded wait).
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 
 #include "join_common.cuh"
 
 namespace knng {
 
 namespace {
-constexpr int kPipeWarps = 8;                       // compute warps
-constexpr int kPipeCompute = 32 * kPipeWarps;       // compute threads
-constexpr int kPipeThreads = kPipeCompute + 32;     // + the producer warp
-constexpr int kPipeSlots = 2;
+// Block shapes (compute warps W, row slots S): four warps with one slot (four
+// blocks per SM, the default) or eight warps with two slots (two per SM).
+constexpr int kPipeMaxSlots = 2;
+template <int W, int S>
+struct PipeShape {
+    static constexpr int kWarps = W;
+    static constexpr int kCompute = 32 * W;
+    static constexpr int kThreads = 32 * (W + 1);
+    static constexpr int kSlots = S;
+    static constexpr int kMinBlocks = W == 8 ? 2 : 4;
+};
 constexpr int kPipeMaxUnits = 64;                   // 16-byte units per row: rows of up to 256 floats
 constexpr uint32_t kPipeHdrBytes = 1024;            // slot header: ns, m | ids[64] | worst keys[64]
 constexpr int kPipeDStride = kSetMax + 1;
@@ -88,15 +97,15 @@ struct PipeCur {
 };
 
 struct PipeShared {
-    uint64_t full[kPipeSlots];
-    uint64_t empty[kPipeSlots];
+    uint64_t full[kPipeMaxSlots];
+    uint64_t empty[kPipeMaxSlots];
     int abort_flag;
     long long stat[8];
 };
 
-__host__ __device__ __forceinline__ size_t pipe_smem_bytes(int nv) {
+__host__ __device__ __forceinline__ size_t pipe_smem_bytes(int nv, int slots) {
     const PipeGeo g = pipe_geo(nv);
-    return 128 + (size_t)kPipeSlots * g.slot_bytes + ((sizeof(PipeCur) + 127) & ~(size_t)127);
+    return 128 + (size_t)slots * g.slot_bytes + ((sizeof(PipeCur) + 127) & ~(size_t)127);
 }
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -144,7 +153,8 @@ __device__ __forceinline__ void cpa8(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }
 // named barrier of the compute warps only
-__device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kPipeCompute) : "memory"); }
+template <int NT>
+__device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
 
 // float4 unit v of row r in a slot's row area
 __device__ __forceinline__ const float4 *pipe_unit(const unsigned char *rows, const PipeGeo &g, int r, int v) {
@@ -155,12 +165,12 @@ __device__ __forceinline__ const float4 *pipe_unit(const unsigned char *rows, co
 // Distance block of the new rows against all rows, RB rows x 4 columns per
 // item: rows a + r MA, columns b + q NB (consecutive threads take consecutive
 // b: consecutive rows, distinct banks; the RB rows are shared by a warp).
-template <int RB>
+template <int RB, int NT>
 __device__ __forceinline__ void pipe_dist(const unsigned char *rows, const PipeGeo &g, float *D, int ns, int m,
                                           int tid) {
     const int MA = (m + RB - 1) / RB, NB = (ns + 3) >> 2, items = MA * NB;
     const uint32_t nbm = div_magic((uint32_t)NB);
-    for (int e = tid; e < items; e += kPipeCompute) {
+    for (int e = tid; e < items; e += NT) {
         const int a = (int)div_small((uint32_t)e, (uint32_t)NB, nbm), b = e - a * NB;
         int ri[RB], cj[4];
         bool vr[RB], vc[4];
@@ -207,7 +217,10 @@ __device__ __forceinline__ void pipe_dist(const unsigned char *rows, const PipeG
 }
 }  // namespace
 
-__global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st, int li) {
+template <int W, int S>
+__global__ void __launch_bounds__(PipeShape<W, S>::kThreads, PipeShape<W, S>::kMinBlocks)
+    pipe_join_kernel(DevState st, int li) {
+    constexpr int kPipeWarps = W, kPipeCompute = 32 * W, kPipeSlots = S;
     if (iteration_skipped(st, li)) return;
     extern __shared__ __align__(128) unsigned char smem[];
     PipeShared *sh = reinterpret_cast<PipeShared *>(smem);
@@ -254,9 +267,9 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
         const unsigned char *X = reinterpret_cast<const unsigned char *>(st.X);
         const size_t row_bytes = (size_t)st.nv * 16;
         for (;;) {
-            const int slot = k & 1;
+            const int slot = k % kPipeSlots;
             unsigned char *sb = slots + (size_t)slot * geo.slot_bytes;
-            if (k >= kPipeSlots && !bar_wait(&sh->empty[slot], ((k >> 1) - 1) & 1, abort_flag)) {
+            if (k >= kPipeSlots && !bar_wait(&sh->empty[slot], (k / kPipeSlots - 1) & 1, abort_flag)) {
                 ok = false;
                 break;
             }
@@ -310,9 +323,9 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
         // ---------------------------------------------------------- compute --
         long long l_evals = 0, l_gath = 0, l_props = 0, l_ovf = 0, l_ins = 0;
         for (int k = 0;; ++k) {
-            const int slot = k & 1;
+            const int slot = k % kPipeSlots;
             const unsigned char *sb = slots + (size_t)slot * geo.slot_bytes;
-            if (!bar_wait(&sh->full[slot], (k >> 1) & 1, abort_flag)) {
+            if (!bar_wait(&sh->full[slot], (k / kPipeSlots) & 1, abort_flag)) {
                 if (tid == 0 && !*abort_flag) {
                     sh->abort_flag = 1;
                     ++w_to;
@@ -332,9 +345,13 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
             // ---- 1. distance block (RB so that the items fill the block)
             const unsigned char *rows = sb + kPipeHdrBytes;
             const int nb = (ns + 3) >> 2;
-            if (((m + 1) >> 1) * nb >= kPipeCompute / 2) pipe_dist<2>(rows, geo, cur->D, ns, m, tid);
-            else pipe_dist<1>(rows, geo, cur->D, ns, m, tid);
-            compute_sync();
+            // 2 x 4 items unless 1 x 4 items finish sooner: the slowest thread
+            // takes ceil(items / threads) items (the others wait at the barrier)
+            const int waves2 = (((m + 1) >> 1) * nb + kPipeCompute - 1) / kPipeCompute;
+            const int waves1 = (m * nb + kPipeCompute - 1) / kPipeCompute;
+            if (8 * waves2 <= 5 * waves1) pipe_dist<2, kPipeCompute>(rows, geo, cur->D, ns, m, tid);
+            else pipe_dist<1, kPipeCompute>(rows, geo, cur->D, ns, m, tid);
+            compute_sync<kPipeCompute>();
             if (tid == 0) bar_arrive(&sh->empty[slot]);  // the rows are no longer read
             if (tid == 0) {
                 l_evals += (long long)m * (m - 1) / 2 + (long long)m * o;
@@ -390,11 +407,11 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
                 }
                 int inc = cnt;
 #pragma unroll
-                for (int o2 = 1; o2 < 8; o2 <<= 1) {
+                for (int o2 = 1; o2 < 32; o2 <<= 1) {
                     const int v = __shfl_up_sync(kFull, inc, o2);
                     if ((int)lane >= o2) inc += v;
                 }
-                const int total_w = __shfl_sync(kFull, inc, 7);
+                const int total_w = __shfl_sync(kFull, inc, 31);
                 const int rb = base - (inc - cnt);
                 l_props += (lane == 0) ? total_w : 0;
                 __threadfence_block();
@@ -405,7 +422,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
                     const int kc = act ? kk : total_w - 1;
                     int q = 0;
 #pragma unroll
-                    for (int step = 4; step > 0; step >>= 1) {
+                    for (int step = 16; step > 0; step >>= 1) {
                         const int v = __shfl_sync(kFull, inc, q + step - 1);
                         if (v <= kc) q += step;
                     }
@@ -453,7 +470,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
                     }
                 }
             }
-            compute_sync();  // cur is reused by the next node
+            compute_sync<kPipeCompute>();  // cur is reused by the next node
         }
         const long long w_props = warp_sum(l_props);
         if (lane == 0 && w_props) atomic_add_ll(&sh->stat[2], w_props);
@@ -483,15 +500,31 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_join_kernel(DevState st,
 
 bool pipe_join_fits(int bf16, int nv) { return !bf16 && nv > 8 && nv <= kPipeMaxUnits; }
 
+namespace {
+template <int W, int S>
+cudaError_t launch_pipe_shape(const DevState &st, int li, cudaStream_t s) {
+    const size_t dyn = pipe_smem_bytes(st.nv, S);
+    auto kern = pipe_join_kernel<W, S>;
+    cudaError_t e = smem_opt_in((const void *)kern, dyn);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_for((const void *)kern, PipeShape<W, S>::kThreads, dyn);
+    kern<<<grid, PipeShape<W, S>::kThreads, dyn, s>>>(st, li);
+    return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_pipe_join(const DevState &st, int li, cudaStream_t s) {
     cudaError_t e = st.u_lo == 0 ? launch_set_kernel(st, li, s) : cudaSuccess;
     if (e != cudaSuccess) return e;
-    const size_t dyn = pipe_smem_bytes(st.nv);
-    e = smem_opt_in((const void *)pipe_join_kernel, dyn);
-    if (e != cudaSuccess) return e;
-    const int grid = grid_for((const void *)pipe_join_kernel, kPipeThreads, dyn);
-    pipe_join_kernel<<<grid, kPipeThreads, dyn, s>>>(st, li);
-    return cudaGetLastError();
+    // four compute warps and one row slot per block, four blocks per SM:
+    // measured against eight warps with two slots (two blocks per SM) on the
+    // 1M x 128 mixture, join per launch 14.4 -> 10.2 ms at rho 0.3 and 29.4 ->
+    // 23.4 ms at rho 0.7, and 1.28 -> 0.71 ms on the 54k x 192 audio shape
+    // (more nodes in flight per SM beat deeper prefetch per block); a test
+    // hook selects the other shape
+    const char *shape = std::getenv("KNNG_TEST_PIPE_SHAPE");
+    if (shape && !std::strcmp(shape, "8x2")) return launch_pipe_shape<8, 2>(st, li, s);
+    return launch_pipe_shape<4, 1>(st, li, s);
 }
 
 }  // namespace knng

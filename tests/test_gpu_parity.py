@@ -748,3 +748,25 @@ def test_join_in_node_range_passes_matches_oracle_bit_exact(path, passes, pool, 
     assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
     assert ch == r["changes"]
     assert stats["dist_evals"] == r["evals"]
+
+
+@pytest.mark.parametrize("shape", ["8x2", "4x1"])
+@pytest.mark.parametrize("n,d,K,rho", [(2000, 200, 20, 1.0), (1500, 33, 16, 0.5)])
+def test_pipelined_join_block_shapes_match_oracle_bit_exact(shape, n, d, K, rho, monkeypatch):
+    """The pipelined kernel's block shapes (compute warps x row slots) give
+    the same iteration, bit for bit against the oracle."""
+    monkeypatch.setenv("KNNG_TEST_JOIN_PATH", "pipe")
+    monkeypatch.setenv("KNNG_TEST_PIPE_SHAPE", shape)
+    x = _int_data(n, d, 3, seed=n + d)
+    ids0, new0 = workloads.random_graph(n, K, seed=n + 1, p_new=0.6)
+    with knng.Context(_cuda(x), K, rho=rho, seed=11, graph=(ids0, new0), iter=0) as c:
+        conv, ch = c.iterate()
+        gi, gd, gf = c.state()
+        stats = c.stats()
+    assert stats["join_path"] == PATH_IDS["pipe"] and stats["set_overflow"] == 0
+    st = oracle.State(x, K, rho, seed=11)
+    st.init_graph(ids0, new0, 0)
+    r = st.iterate()
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    assert ch == r["changes"]
