@@ -209,10 +209,26 @@ def measured_traffic(kernel: str):
         return None
 
 
+def deal_by_cost(costs, ranks: int):
+    """Data sets dealt over ranks by their cost (n * d, the work of a build
+    grows with both): largest first, each to the rank with the least load so
+    far (longest-processing-time rule; the heaviest rank carries at most the
+    mean load plus one data set's cost).  Returns, per rank, its data-set
+    indices in ascending order."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * ranks
+    out = [[] for _ in range(ranks)]
+    for i in order:
+        r = min(range(ranks), key=lambda k: (load[k], k))
+        out[r].append(i)
+        load[r] += costs[i]
+    return [sorted(x) for x in out]
+
+
 def run_batched(args):
     """256 independent data sets: one batched build (one launch per step for
     all data sets of a row-width class) against 256 sequential float32
-    builds.  With N ranks the data sets are dealt out round-robin (no
+    builds.  With N ranks the data sets are dealt out by cost, n * d (no
     collective: they are independent), and the step time is the slowest
     rank's."""
     import torch
@@ -228,7 +244,8 @@ def run_batched(args):
         dist.init_process_group("nccl", device_id=device)
     cfg = workloads.BATCHED
     all_sets = workloads.batched_data(cfg["count"], cfg["seed"])
-    sets = all_sets[rank::ws]
+    mine = deal_by_cost([x.shape[0] * x.shape[1] for x in all_sets], ws)[rank]
+    sets = [all_sets[i] for i in mine]
     xs = [torch.from_numpy(x).to(device) for x in sets]
     flags = (knng.FLAG_BF16 if args.bf16 else 0) | (knng.FLAG_GRAPH if args.graph else 0) | \
         (knng.FLAG_AUTOTUNE if args.autotune else 0)
@@ -295,7 +312,7 @@ def run_batched(args):
                    "total_n": int(sum(len(x) for x in all_sets)), "K": K, "rho": rho, "delta": delta,
                    "max_iters": it, "bf16": bool(args.bf16), "graph": bool(args.graph),
                    "autotune": bool(args.autotune),
-                   "parallelism": f"datasets round-robin over {ws} rank(s)",
+                   "parallelism": f"data sets dealt over {ws} rank(s) by n*d (largest first, least-loaded rank)",
                    "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
         "e2e": {"value": round(ve, 6), "unit": "s", "h2d_bytes_per_step": int(sum(x.nbytes for x in sets)),
                 "d2h_bytes_per_step": int(sum(len(x) for x in sets) * K * 8)},
@@ -710,6 +727,8 @@ def run_gpu(args):
             "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
             "bytes_per_launch": round(jb), "launch_ms": round(jt * 1e3, 4), "launches": ran,
+            "launch": "one iteration's local join: the set kernel and every node-range pass of the join "
+                      "kernel (list merges excluded), CUDA events on the library's stream",
             "time_share_join_merge_ms": [round(tst["join_ms_ran"], 3), round(tst["merge_ms_ran"], 3)],
             "step_share": round((kern[name][1] / 1e3) / step_s, 3)}
     l2_gbs = knng.measure_l2_read(32 << 20, 200)

@@ -98,15 +98,17 @@ typedef struct knng_stats {
     int64_t proposals;         /* proposal keys the local join handed to the list merge */
     int64_t bucket_overflow;   /* proposals past a full bucket (inserted under a lock) */
     int32_t reordered;         /* 1 once Algorithm 1 relabelled the points */
-    int32_t join_launches;     /* local-join launches timed (KNNG_FLAG_TIMING) */
-    double join_ms;            /* their summed CUDA-event time */
-    int32_t join_ran;          /* timed launches whose iteration ran (not skipped) */
+    int32_t join_launches;     /* iterations whose local join was timed (KNNG_FLAG_TIMING) */
+    double join_ms;            /* their summed CUDA-event time: every join pass of an iteration
+                                  (an iteration with many candidates runs its join over node
+                                  ranges, a list merge after each), merges excluded */
+    int32_t join_ran;          /* timed iterations that ran (not skipped) */
     int32_t join_path;         /* local-join kernel: 0 warp per node (float32 rows of up to 32
                                   floats), 1 block-per-node tiles, 2 ring of nodes in flight
                                   (bf16 rows), 3 pipelined block per node (float32 rows of 33
                                   to 256 floats) */
-    double join_ms_ran;        /* summed join-kernel time of those iterations */
-    double merge_ms_ran;       /* summed list-merge-kernel time of those iterations */
+    double join_ms_ran;        /* summed join-kernel time of those iterations (all passes) */
+    double merge_ms_ran;       /* summed list-merge-kernel time of those iterations (all passes) */
     double sample_ms_ran;      /* summed selection-step time (degree count + sampling kernels) of
                                   those iterations (KNNG_FLAG_TIMING) */
     double reorder_ms;         /* summed relabelling time, permutation of rows and lists included

@@ -147,9 +147,13 @@ struct knng_ctx {
     std::vector<cudaGraphExec_t> graphs;  // captured iteration loops (KNNG_FLAG_GRAPH)
     cudaStream_t capture = nullptr;       // private stream the loops are captured on
 
-    std::vector<cudaEvent_t> ev;  // per timed iteration: before count, after sampling, before join,
-                                  // after join, after merge
+    std::vector<cudaEvent_t> ev;  // per timed iteration: before the count, after the sampling
     std::vector<int> ev_li;       // iteration index of each pair
+    struct PassEvents {
+        int li;
+        cudaEvent_t join0, join1, merge1;  // before and after a join pass, after its merge
+    };
+    std::vector<PassEvents> pev;  // per timed join pass
     std::vector<cudaEvent_t> rev; // start/stop pairs around relabellings (KNNG_FLAG_TIMING)
 
     DevState dev(bool gate) const {
@@ -526,7 +530,7 @@ int enqueue_iteration(knng_ctx *c, bool gate) {
     const int li = c->li, it = c->it_done + 1;
     DevState st = c->dev(gate);
     const bool timing = (c->flags & KNNG_FLAG_TIMING) != 0;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     if (timing) {
         for (auto &e : ev) KNNG_TRY(cudaEventCreate(&e));
         for (auto &e : ev) c->ev.push_back(e);
@@ -542,7 +546,6 @@ int enqueue_iteration(knng_ctx *c, bool gate) {
         if (rc) return rc;
         st = c->dev(gate);
     }
-    if (timing) KNNG_TRY(cudaEventRecord(ev[2], c->stream));
     // the join in node-range passes, each followed by a list merge, so that
     // one pass's proposals fit the buckets and the pool (the set kernel runs
     // with the first pass; later passes filter against the merged lists)
@@ -550,12 +553,20 @@ int enqueue_iteration(knng_ctx *c, bool gate) {
     for (int p = 0; p < passes; ++p) {
         st.u_lo = c->n * p / passes;
         st.u_hi = c->n * (p + 1) / passes;
+        knng_ctx::PassEvents pe{li, nullptr, nullptr, nullptr};
+        if (timing) {
+            KNNG_TRY(cudaEventCreate(&pe.join0));
+            KNNG_TRY(cudaEventCreate(&pe.join1));
+            KNNG_TRY(cudaEventCreate(&pe.merge1));
+            c->pev.push_back(pe);
+            KNNG_TRY(cudaEventRecord(pe.join0, c->stream));
+        }
         KNNG_TRY(launch_join(st, li, c->stream));
-        if (p + 1 == passes && timing) KNNG_TRY(cudaEventRecord(ev[3], c->stream));
+        if (timing) KNNG_TRY(cudaEventRecord(pe.join1, c->stream));
         KNNG_TRY(launch_merge(st, li, c->stream));
+        if (timing) KNNG_TRY(cudaEventRecord(pe.merge1, c->stream));
         if (p + 1 < passes) KNNG_TRY(cudaMemsetAsync(c->pool_next, 0, sizeof(int), c->stream));
     }
-    if (timing) KNNG_TRY(cudaEventRecord(ev[4], c->stream));
     c->launches += (c->heap ? 4 : 2) + passes * (1 + join_launches(c->join_path)) - (passes - 1) *
                    (join_launches(c->join_path) - 1);
     c->li++;
@@ -834,18 +845,27 @@ int knng_get_stats(knng_ctx *c, knng_stats *out) {
     out->join_ms_ran = 0;
     out->merge_ms_ran = 0;
     out->sample_ms_ran = 0;
-    for (size_t i = 0; i + 4 < c->ev.size(); i += 5) {
-        float ms0 = 0, ms = 0, ms2 = 0;
-        if (cudaEventElapsedTime(&ms0, c->ev[i], c->ev[i + 1]) == cudaSuccess &&
-            cudaEventElapsedTime(&ms, c->ev[i + 2], c->ev[i + 3]) == cudaSuccess &&
-            cudaEventElapsedTime(&ms2, c->ev[i + 3], c->ev[i + 4]) == cudaSuccess) {
-            out->join_ms += ms;
+    for (size_t i = 0; i + 1 < c->ev.size(); i += 2) {
+        float ms0 = 0;
+        const bool ran = its[(size_t)c->ev_li[i / 2] * kItCount + kItRan] != 0;
+        if (cudaEventElapsedTime(&ms0, c->ev[i], c->ev[i + 1]) == cudaSuccess) {
             out->join_launches++;
-            if (its[(size_t)c->ev_li[i / 5] * kItCount + kItRan]) {
+            if (ran) {
                 out->sample_ms_ran += ms0;
+                out->join_ran++;
+            }
+        } else {
+            cudaGetLastError();
+        }
+    }
+    for (const auto &pe : c->pev) {
+        float ms = 0, ms2 = 0;
+        if (cudaEventElapsedTime(&ms, pe.join0, pe.join1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms2, pe.join1, pe.merge1) == cudaSuccess) {
+            out->join_ms += ms;
+            if (its[(size_t)pe.li * kItCount + kItRan]) {
                 out->join_ms_ran += ms;
                 out->merge_ms_ran += ms2;
-                out->join_ran++;
             }
         } else {
             cudaGetLastError();
@@ -869,6 +889,11 @@ int knng_destroy(knng_ctx *c) {
     }
     if (c->capture) cudaStreamDestroy(c->capture);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (const auto &pe : c->pev) {
+        cudaEventDestroy(pe.join0);
+        cudaEventDestroy(pe.join1);
+        cudaEventDestroy(pe.merge1);
+    }
     for (cudaEvent_t e : c->rev) cudaEventDestroy(e);
     if (c->arena) cudaFreeAsync(c->arena, c->stream);
     if (c->barena) cudaFreeAsync(c->barena, c->stream);

@@ -41,3 +41,27 @@ def test_workload_overrides_are_named():
     w, x, name = bench._workload(A())
     assert (w.n, w.rho, w.max_iters) == (500, 0.5, 4) and x.shape == (500, 8)
     assert name == "uniform_n2k_d8_n500_rho0.5_max_iters4"
+
+
+@pytest.mark.parametrize("ranks", [1, 2, 3, 8])
+def test_batched_data_sets_dealt_by_cost(ranks):
+    """Every data set of the batched workload lands on exactly one rank, and
+    the heaviest rank's n*d load is within one data set of the mean."""
+    import workloads
+    specs = workloads.batched_specs(256, 0)
+    costs = [s["n"] * s["d"] for s in specs]
+    parts = bench.deal_by_cost(costs, ranks)
+    assert len(parts) == ranks
+    flat = sorted(i for p in parts for i in p)
+    assert flat == list(range(len(costs)))
+    loads = [sum(costs[i] for i in p) for p in parts]
+    assert max(loads) <= sum(costs) / ranks + max(costs)
+    if ranks > 1:
+        # the deal is balanced far better than round-robin's worst case
+        assert max(loads) - min(loads) <= max(costs)
+
+
+def test_deal_by_cost_hand_case():
+    """Largest first to the least-loaded rank: costs 7, 5, 4, 3, 1 over two
+    ranks give {7, 3} and {5, 4, 1}, loads 10 and 10."""
+    assert bench.deal_by_cost([4, 7, 1, 5, 3], 2) == [[1, 4], [0, 2, 3]]

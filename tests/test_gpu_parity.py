@@ -770,3 +770,28 @@ def test_pipelined_join_block_shapes_match_oracle_bit_exact(shape, n, d, K, rho,
     oi, od, of = st.state()
     assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
     assert ch == r["changes"]
+
+
+@pytest.mark.parametrize("n,d,K,rho,bf16", [(900, 1600, 16, 0.5, False), (900, 2000, 16, 0.5, True),
+                                            (700, 3144, 12, 0.5, False)])
+def test_wide_rows_match_oracle_bit_exact(n, d, K, rho, bf16):
+    """Row widths the dimension sweep times (up to the paper's d = 3144),
+    beyond the ring and pipelined kernels: the block-per-node tile kernel in
+    float32 and with bf16 tensor-core Gram blocks, one iteration bit-exact
+    against the oracle on small integers (every product and partial sum
+    exact in float32, so the bf16 expansion equals the difference form)."""
+    x = _int_data(n, d, 3, seed=d)
+    ids0, new0 = workloads.random_graph(n, K, seed=n + 5, p_new=0.6)
+    flags = knng.FLAG_BF16 if bf16 else 0
+    with knng.Context(_cuda(x), K, rho=rho, seed=13, graph=(ids0, new0), iter=0, flags=flags) as c:
+        conv, ch = c.iterate()
+        gi, gd, gf = c.state()
+        stats = c.stats()
+    assert stats["join_path"] == PATH_IDS["tile"]
+    assert stats["set_overflow"] == 0 and stats["lock_timeouts"] == 0
+    st = oracle.State(x, K, rho, seed=13)
+    st.init_graph(ids0, new0, 0)
+    r = st.iterate()
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    assert ch == r["changes"]
