@@ -633,10 +633,15 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     flags = (knng.FLAG_REORDER if args.reorder else 0) | (knng.FLAG_BF16 if args.bf16 else 0) | \
         (knng.FLAG_GRAPH if args.graph else 0) | (knng.FLAG_AUTOTUNE if args.autotune else 0) | \
-        (knng.FLAG_HEAP_SAMPLING if args.heap else 0) | \
+        (knng.FLAG_HEAP_SAMPLING if args.heap else 0) | (knng.FLAG_FP8 if args.fp8 else 0) | \
         (knng.FLAG_REORDER | knng.FLAG_REORDER_PARALLEL if args.reorder_parallel else 0)
-    bf16_rows = args.bf16 and w.d >= 64
-    dp = (w.d + 63) // 64 * 64 // 2 if bf16_rows else (w.d + 3) // 4 * 4  # float32 words per gathered row
+    # float32 words per gathered row (bf16 rows: 2 bytes an element, e4m3: 1)
+    if args.fp8 and w.d >= 64:
+        dp = (w.d + 63) // 64 * 64 // 4
+    elif args.bf16 and w.d >= 64:
+        dp = (w.d + 63) // 64 * 64 // 2
+    else:
+        dp = (w.d + 3) // 4 * 4
 
     with ClockSampler(local) as clk:
         step_s, (ids, dists, stats) = _time_builds(knng, xd, op, flags, args.steps, args.warmup, flush, stream, ws)
@@ -700,9 +705,10 @@ def run_gpu(args):
                   for (r, dl, it) in LADDER.get(args.workload, [])]
         stated = next((q for q in ladder if (q["rho"], q["delta"], q["max_iters"]) == (w.rho, w.delta, w.max_iters)),
                       None)
-        if w.d >= 64 and not args.bf16:
+        if w.d >= 64 and not (args.bf16 or args.fp8):
             bf16_form = {"at_timed_point": point(op, flags | knng.FLAG_BF16),
-                         "at_stated_parameters": point(w, flags | knng.FLAG_BF16)}
+                         "at_stated_parameters": point(w, flags | knng.FLAG_BF16),
+                         "fp8_at_timed_point": point(op, flags | knng.FLAG_FP8)}
 
     # the metric's recall condition
     recall_ok = min(rec_seeds) >= 0.99
@@ -722,7 +728,7 @@ def run_gpu(args):
     jb = kern[name][0] / ran
     jt = kern[name][1] / 1e3 / ran
     achieved = jb / jt / 1e9
-    traffic = measured_traffic(f"{name}@{wname}" + ("+bf16" if args.bf16 else ""))
+    traffic = measured_traffic(f"{name}@{wname}" + ("+fp8" if args.fp8 else "+bf16" if args.bf16 else ""))
     roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
             "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
@@ -740,12 +746,14 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": round(step_s, 6), "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 4), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if args.bf16 else "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp8+f32" if args.fp8 else ("bf16+f32" if args.bf16 else "f32"), "data": "synthetic",
         "config": {"workload": wname, "n": w.n, "d": w.d, "K": w.K, "rho": op.rho, "delta": op.delta,
                    "max_iters": op.max_iters,
                    "stated_parameters": {"rho": w.rho, "delta": w.delta, "max_iters": w.max_iters},
                    "reorder": "parallel" if args.reorder_parallel else ("algorithm1" if args.reorder else False),
-                   "bf16": bool(args.bf16), "graph": bool(args.graph), "autotune": bool(args.autotune),
+                   "bf16": bool(args.bf16), "fp8": bool(args.fp8), "graph": bool(args.graph),
+                   "autotune": bool(args.autotune),
                    "join_path": stats["join_path"], "sampler": "heap" if args.heap else "turbo",
                    "parallelism": f"replicas{ws}",
                    "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
@@ -914,6 +922,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--reorder", action="store_true", help="Algorithm 1 relabelling after iteration 1")
     ap.add_argument("--bf16", action="store_true", help="bf16 tensor-core dots for d >= 64, float32 re-rank")
+    ap.add_argument("--fp8", action="store_true", help="e4m3 tensor-core dots for d >= 64 (lossy), float32 re-rank")
     ap.add_argument("--graph", action="store_true", help="launch the iteration loop as one captured CUDA graph")
     ap.add_argument("--autotune", action="store_true", help="time the join kernels on the first build, keep the fastest")
     ap.add_argument("--reorder-parallel", action="store_true",

@@ -70,6 +70,11 @@ extern "C" {
                                         the s smallest (priority, id) offers, one per id; forward new
                                         entries kept as new candidates lose their flag; requires
                                         n * K < 2^31 (else KNNG_ERR_UNSUPPORTED) */
+#define KNNG_FLAG_FP8 0x100u /* d >= 64, rows that fit the ring join kernel: local-join dots in FP8 (e4m3 rows,
+                                rounded to nearest and saturated at +-448, float32 accumulate on the tensor
+                                cores, |x|^2+|y|^2-2x.y with the norms of the e4m3 values); output re-ranked
+                                in float32.  Lossy beyond 4 significant bits (integers up to 16 are exact,
+                                larger ones round); takes precedence over KNNG_FLAG_BF16 */
 #define KNNG_FLAG_REORDER_PARALLEL 0x80u /* with REORDER: relabel by the data-parallel variant instead of
                                            Algorithm 1 -- single-linkage (Boruvka) rounds on the list graph,
                                            edges ordered by (float32 distance, min id, max id), every

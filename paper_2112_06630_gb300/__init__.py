@@ -19,7 +19,7 @@ from . import build as _build
 __all__ = [
     "KnngError", "Stats", "Context", "knng_build", "knng_build_batched", "knng_bruteforce", "lib_path", "Desc",
     "bruteforce_last_fallbacks", "bruteforce_last_prefilter_ms", "measure_l2_read",
-    "FLAG_REORDER", "FLAG_REORDER_B", "FLAG_TIMING", "FLAG_GRAPH", "FLAG_BF16", "FLAG_AUTOTUNE", "FLAG_HEAP_SAMPLING", "FLAG_REORDER_PARALLEL", "version", "strerror", "load",
+    "FLAG_REORDER", "FLAG_REORDER_B", "FLAG_TIMING", "FLAG_GRAPH", "FLAG_BF16", "FLAG_AUTOTUNE", "FLAG_HEAP_SAMPLING", "FLAG_REORDER_PARALLEL", "FLAG_FP8", "version", "strerror", "load",
 ]
 
 FLAG_REORDER = 0x1
@@ -30,6 +30,7 @@ FLAG_BF16 = 0x10
 FLAG_AUTOTUNE = 0x20
 FLAG_HEAP_SAMPLING = 0x40
 FLAG_REORDER_PARALLEL = 0x80
+FLAG_FP8 = 0x100
 
 OK = 0
 WARN_OVERFLOW = 1

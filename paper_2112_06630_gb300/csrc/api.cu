@@ -131,6 +131,9 @@ struct knng_ctx {
     float *xnorm = nullptr, *xnorm2 = nullptr;
     int dpb = 0;
     bool bf16 = false;
+    bool fp8 = false;  // KNNG_FLAG_FP8 taken: e4m3 rows in Xb
+    // precision of the join's rows: 0 float32, 1 bf16, 2 e4m3
+    int kind() const { return fp8 ? 2 : bf16 ? 1 : 0; }
     int join_path = kJoinWarp;
     int *cset = nullptr, *cmeta = nullptr;
     uint64_t *pbucket = nullptr, *ppool = nullptr;
@@ -186,7 +189,8 @@ struct knng_ctx {
         st.d = d;
         st.dp = dp;
         st.dpb = dpb;
-        st.bf16 = bf16 ? 1 : 0;
+        st.bf16 = (bf16 || fp8) ? 1 : 0;
+        st.fp8 = fp8 ? 1 : 0;
         st.nv = nv;
         st.K = K;
         st.s = s;
@@ -218,7 +222,7 @@ thread_local float g_bf_prefilter_ms = -1.f;
 std::mutex g_tune_mu;
 std::map<std::array<int, 4>, int> g_tune_cache;
 
-std::array<int, 4> tune_key(const knng_ctx *c) { return {c->bf16 ? 1 : 0, c->bf16 ? c->dpb : c->dp, c->K, c->R}; }
+std::array<int, 4> tune_key(const knng_ctx *c) { return {c->kind(), c->kind() ? c->dpb : c->dp, c->K, c->R}; }
 
 int ctx_alloc(knng_ctx *c) {
     const int64_t n = c->n;
@@ -244,11 +248,11 @@ int ctx_alloc(knng_ctx *c) {
     const size_t oS = take(sizeof(long long) * kStatCount);
     const size_t oT = take(sizeof(long long) * kItCount * kMaxLocalIters);
     const size_t oE = take(sizeof(int));
-    const size_t oXb = c->bf16 ? take(sizeof(uint16_t) * n * c->dpb) : 0;
-    const size_t oXn = c->bf16 ? take(sizeof(float) * n) : 0;
+    const size_t oXb = c->fp8 ? take((size_t)n * c->dpb) : c->bf16 ? take(sizeof(uint16_t) * n * c->dpb) : 0;
+    const size_t oXn = (c->bf16 || c->fp8) ? take(sizeof(float) * n) : 0;
     const bool ring = c->join_path == kJoinRing || c->join_path == kJoinPipe ||
-                      (c->tune_pending && (ring_join_fits(c->bf16, c->nv, c->dpb, c->K) ||
-                                           pipe_join_fits(c->bf16, c->nv)));
+                      (c->tune_pending && (ring_join_fits(c->kind(), c->nv, c->dpb, c->K) ||
+                                           pipe_join_fits(c->kind(), c->nv)));
     const size_t oCs = ring ? take(sizeof(int) * (size_t)n * kSetMax) : 0;
     const size_t oCm = ring ? take(sizeof(int) * (size_t)n) : 0;
     const bool prel = reorder && (c->flags & KNNG_FLAG_REORDER_PARALLEL);
@@ -283,7 +287,7 @@ int ctx_alloc(knng_ctx *c) {
     c->stats = (long long *)(a + oS);
     c->it_stats = (long long *)(a + oT);
     c->err = (int *)(a + oE);
-    if (c->bf16) {
+    if (c->bf16 || c->fp8) {
         c->Xb = (uint16_t *)(a + oXb);
         c->xnorm = (float *)(a + oXn);
     }
@@ -312,6 +316,20 @@ int ctx_alloc(knng_ctx *c) {
     return KNNG_OK;
 }
 
+// The low-precision copy of the staged rows the join reads, if any.
+cudaError_t stage_low_precision(knng_ctx *c) {
+    if (c->fp8) {
+        c->launches++;
+        return launch_stage_fp8(c->X, c->n, c->dp, c->d, reinterpret_cast<uint8_t *>(c->Xb), c->dpb, c->xnorm,
+                                c->stream);
+    }
+    if (c->bf16) {
+        c->launches++;
+        return launch_stage_bf16(c->X, c->n, c->dp, c->d, c->Xb, c->dpb, c->xnorm, c->stream);
+    }
+    return cudaSuccess;
+}
+
 // Stage the caller's points (host or device) into the padded layout.
 int ctx_stage(knng_ctx *c, const float *data) {
     const size_t bytes = sizeof(float) * c->n * c->d;
@@ -324,10 +342,7 @@ int ctx_stage(knng_ctx *c, const float *data) {
     }
     KNNG_TRY(launch_stage(src, c->n, c->d, c->X, c->dp, c->stream));
     c->launches++;
-    if (c->bf16) {
-        KNNG_TRY(launch_stage_bf16(c->X, c->n, c->dp, c->d, c->Xb, c->dpb, c->xnorm, c->stream));
-        c->launches++;
-    }
+    KNNG_TRY(stage_low_precision(c));
     if (tmp) KNNG_TRY(cudaFreeAsync(tmp, c->stream));
     return KNNG_OK;
 }
@@ -368,6 +383,10 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
         return KNNG_ERR_UNSUPPORTED;
     }
     c->dpb = (d + 63) & ~63;
+    // FP8 (e4m3) rows where the ring kernel holds them (it is their only join
+    // kernel); otherwise the flag is not taken
+    c->fp8 = (flags & KNNG_FLAG_FP8) && d >= 64 && ring_join_fits(2, c->nv, c->dpb, K);
+    if (c->fp8) c->bf16 = false;
     // test hook: run another join kernel the context can use (parity of the
     // three kernels on the same inputs)
     int force = -1;
@@ -377,7 +396,7 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
         else if (!std::strcmp(e, "ring")) force = kJoinRing;
         else if (!std::strcmp(e, "pipe")) force = kJoinPipe;
     }
-    c->join_path = choose_join_path(c->bf16, c->nv, c->dpb, K, force);
+    c->join_path = choose_join_path(c->kind(), c->nv, c->dpb, K, force);
     if ((flags & KNNG_FLAG_AUTOTUNE) && force < 0) {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(tune_key(c));
@@ -439,10 +458,7 @@ int enqueue_reorder(knng_ctx *c) {
     if (ev[1]) KNNG_TRY(cudaEventRecord(ev[1], c->stream));
     std::swap(c->X, c->X2);
     std::swap(c->keys, c->keys2);
-    if (c->bf16) {
-        KNNG_TRY(launch_stage_bf16(c->X, c->n, c->dp, c->d, c->Xb, c->dpb, c->xnorm, c->stream));
-        c->launches++;
-    }
+    KNNG_TRY(stage_low_precision(c));
     c->reordered = true;
     return KNNG_OK;
 }
@@ -454,10 +470,11 @@ int enqueue_reorder(knng_ctx *c) {
 // the lists (which a full bucket's locked insertion may touch), the global
 // counters and the iteration's counters restored.  Synchronises the stream.
 int autotune_join(knng_ctx *c, int li) {
-    std::vector<int> paths = {kJoinTile};
-    if (!c->bf16) paths.push_back(kJoinWarp);
-    if (ring_join_fits(c->bf16, c->nv, c->dpb, c->K) && c->cset) paths.push_back(kJoinRing);
-    if (pipe_join_fits(c->bf16, c->nv) && c->cset) paths.push_back(kJoinPipe);
+    std::vector<int> paths;
+    if (c->kind() < 2) paths.push_back(kJoinTile);
+    if (c->kind() == 0) paths.push_back(kJoinWarp);
+    if (ring_join_fits(c->kind(), c->nv, c->dpb, c->K) && c->cset) paths.push_back(kJoinRing);
+    if (pipe_join_fits(c->kind(), c->nv) && c->cset) paths.push_back(kJoinPipe);
     const size_t kb = sizeof(uint64_t) * (size_t)c->n * c->K;
     unsigned char *tmp = nullptr;
     KNNG_TRY(lib_malloc((void **)&tmp, align256(kb) + sizeof(long long) * kStatCount, c->stream));
@@ -993,9 +1010,9 @@ int build_batched_group(const knng_desc *descs, int count, int K, float rho, flo
         if (e == cudaSuccess) e = launch_stage(src, d.n, d.d, c->X + (size_t)off[b] * c->dp, c->dp, s);
         if (tmp) cudaFreeAsync(tmp, s);
     }
-    if (e == cudaSuccess && c->bf16) e = launch_stage_bf16(c->X, ntot, c->dp, dmax, c->Xb, c->dpb, c->xnorm, s);
+    if (e == cudaSuccess) e = stage_low_precision(c);
     if (e == cudaSuccess) e = launch_init_random(c->dev(false), seed, c->err, s);
-    c->launches += count + 3;
+    c->launches += count + 2;
     if (e != cudaSuccess) {
         knng_destroy(c);
         return cuda_code(e);

@@ -185,8 +185,9 @@ enum ItStat : int {
 
 struct DevState {
     const float *X;      // n x dp, zero padded
-    const uint16_t *Xb;  // n x dpb bf16 bits (zero padded to a multiple of 64), bf16 mode only
-    const float *xnorm;  // n squared norms of the bf16 rows, bf16 mode only
+    const uint16_t *Xb;  // n x dpb bf16 bits (zero padded to a multiple of 64), bf16 mode only;
+                         // in FP8 mode n x dpb e4m3 bytes
+    const float *xnorm;  // n squared norms of the bf16 (or e4m3) rows, low-precision modes only
     uint64_t *keys;      // n x K, ascending
     int *locks;          // n, taken only when a proposal bucket is full
     int *pcursor;        // n, proposals reserved in each node's bucket this iteration
@@ -208,7 +209,9 @@ struct DevState {
     long long *it_stats;       // (max_iters + 2) x kItCount
     int64_t n;
     int d, dp, nv, K, s, R, cap, dpb;
-    int bf16;                  // 1: high-d joins use bf16 tensor-core Gram blocks
+    int bf16;                  // 1: high-d joins use low-precision tensor-core Gram blocks (bf16 or
+                               // FP8): list keys are not the canonical float32 distances
+    int fp8;                   // 1: the low-precision rows are e4m3 (FP8 mode)
     // batched mode (many independent data sets in one node space), else null:
     const int *ds;             // node -> data set
     const long long *ds_off;   // data set -> first node

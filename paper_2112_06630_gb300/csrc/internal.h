@@ -56,6 +56,10 @@ int choose_join_path(int bf16, int nv, int dpb, int K, int force);
 int join_launches(int path);
 cudaError_t launch_stage_bf16(const float *X, int64_t n, int dp, int d, uint16_t *Xb, int dpb, float *nrm,
                               cudaStream_t s);
+// e4m3 copy of the rows (round to nearest, saturating at +-448) and the
+// squared norms of the e4m3 values
+cudaError_t launch_stage_fp8(const float *X, int64_t n, int dp, int d, uint8_t *X8, int dpb, float *nrm,
+                             cudaStream_t s);
 cudaError_t launch_greedy_reorder(const uint64_t *keys, int64_t n, int K, int reading_b, int32_t *sigma,
                                   int32_t *sigma_inv, cudaStream_t s);
 cudaError_t launch_permute(const DevState &src, float *X_dst, uint64_t *keys_dst, const int32_t *sigma,

@@ -534,6 +534,8 @@ cudaError_t launch_join_t(const DevState &st, int li, cudaStream_t s) {
 }  // namespace
 
 int choose_join_path(int bf16, int nv, int dpb, int K, int force) {
+    // FP8 rows (kind 2) have only the ring kernel (the caller checks the fit)
+    if (bf16 == 2) return kJoinRing;
     const bool ring = ring_join_fits(bf16, nv, dpb, K);
     const bool pipe = pipe_join_fits(bf16, nv);
     if (force == kJoinWarp && !bf16) return kJoinWarp;

@@ -70,9 +70,11 @@ __host__ __device__ __forceinline__ uint32_t align_up(uint32_t x, uint32_t a) { 
 struct Geometry {
     uint32_t gbytes, stride;
 };
-__host__ __device__ __forceinline__ Geometry geometry(int bf16, int nv, int dpb) {
+// kind: 0 float32 rows (nv 16-byte units), 1 bf16 rows of dpb elements, 2
+// e4m3 rows of dpb elements (one byte each)
+__host__ __device__ __forceinline__ Geometry geometry(int kind, int nv, int dpb) {
     Geometry g;
-    const uint32_t units = bf16 ? (uint32_t)dpb / 8u : (uint32_t)nv;
+    const uint32_t units = kind == 2 ? (uint32_t)dpb / 16u : kind == 1 ? (uint32_t)dpb / 8u : (uint32_t)nv;
     g.gbytes = units * 16u;
     g.stride = (units | 1u) * 16u;
     return g;
@@ -296,6 +298,57 @@ __device__ __forceinline__ void warp_gram_bf16(const unsigned char *rows, uint32
             }
     }
 }
+// The same Gram block from e4m3 rows (FP8, one byte per element): 32
+// elements per k-step, mma.sync m16n8k32 e4m3 with float32 accumulate.  The
+// fragments of a 32-byte k-step have the layout of a bf16 m16n8k16 step (four
+// consecutive bytes where bf16 has two elements), so the ldmatrix addressing
+// is the bf16 one.
+__device__ __forceinline__ void warp_gram_fp8(const unsigned char *rows, uint32_t stride, const float *nrm,
+                                              float *D, int ds, int ns, int m, int dpb) {
+    const unsigned lane = lane_id();
+    const int nk = dpb / 32, ntiles = (ns + 7) >> 3;
+    const int gid = lane >> 2, tig = lane & 3;
+    for (int r0 = 0; r0 < m; r0 += 16) {
+        float acc[8][4];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+        const int ar = min(r0 + (int)(lane & 15), ns - 1), ac = 16 * (int)(lane >> 4);
+        const uint32_t abase = smem_u32(rows + (size_t)ar * stride) + ac;
+        uint32_t bbase[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int br = min(q * 8 + (int)(lane & 7), ns - 1), bc = 16 * (int)((lane >> 3) & 1);
+            bbase[q] = smem_u32(rows + (size_t)br * stride) + bc;
+        }
+        for (int kk = 0; kk < nk; ++kk) {
+            uint32_t a0, a1, a2, a3;
+            asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                         : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
+                         : "r"(abase + kk * 32));
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q < ntiles) {
+                    uint32_t b0, b1;
+                    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                                 : "=r"(b0), "=r"(b1)
+                                 : "r"(bbase[q] + kk * 32));
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                        "{%8,%9}, {%0,%1,%2,%3};\n"
+                        : "+f"(acc[q][0]), "+f"(acc[q][1]), "+f"(acc[q][2]), "+f"(acc[q][3])
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int i = r0 + gid + 8 * (h >> 1), j = q * 8 + tig * 2 + (h & 1);
+                if (q < ntiles && i < m && j < ns) D[i * ds + j] = fmaxf(0.f, nrm[i] + nrm[j] - 2.f * acc[q][h]);
+            }
+    }
+}
 }  // namespace
 
 // ------------------------------------------------------------ set_kernel --
@@ -338,7 +391,7 @@ namespace {
 // Copies of a node's candidate rows, worst keys (and bf16 norms) into its
 // slots, issued by the consumer warp that runs the node, as one cp.async
 // group per lane.
-template <bool kBF16>
+template <int kKind>
 __device__ __forceinline__ void issue_copies(const DevState &st, const Geometry &geo, const unsigned char *src,
                                              unsigned char *sa, unsigned char *sb, const SlotB &LB, int ns) {
     const unsigned lane = lane_id();
@@ -353,18 +406,19 @@ __device__ __forceinline__ void issue_copies(const DevState &st, const Geometry 
     }
     for (int i = lane; i < ns; i += 32) {
         cp_async8(sb + LB.o_swk + 8 * i, st.keys + (size_t)sid[i] * K + (K - 1));
-        if (kBF16) cp_async4(sb + LB.o_nrm + 4 * i, st.xnorm + sid[i]);
+        if (kKind != 0) cp_async4(sb + LB.o_nrm + 4 * i, st.xnorm + sid[i]);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 }  // namespace
 
-template <bool kBF16>
+template <int kKind>
 __global__ void __launch_bounds__(kRingThreads, 1) ring_join_kernel(DevState st, int li) {
+    constexpr bool kBF16 = kKind != 0;  // low-precision rows: Gram blocks with norms
     if (iteration_skipped(st, li)) return;
     __shared__ RingShared sh;
     extern __shared__ __align__(128) unsigned char ring[];
-    const Geometry geo = geometry(kBF16, st.nv, st.dpb);
+    const Geometry geo = geometry(kKind, st.nv, st.dpb);
     const uint32_t ring_b_cap = ring_b_bytes(geo), ring_a_cap = kRingBytes - ring_b_cap;
     unsigned char *ring_a = ring, *ring_b = ring + ring_a_cap;
     const unsigned lane = lane_id();
@@ -515,7 +569,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) ring_join_kernel(DevState st,
         };
         auto start = [&](int k, int nsm) {
             const int s = k % kRingDesc, ns = nsm & 0xFF, m = (nsm >> 8) & 0xFF;
-            issue_copies<kBF16>(st, geo, src, ring_a + sh.desc[s].off_a, ring_b + sh.desc[s].off_b, slot_b(ns, m),
+            issue_copies<kKind>(st, geo, src, ring_a + sh.desc[s].off_a, ring_b + sh.desc[s].off_b, slot_b(ns, m),
                                 ns);
         };
         bool ok = true;
@@ -541,7 +595,8 @@ __global__ void __launch_bounds__(kRingThreads, 1) ring_join_kernel(DevState st,
             const int ds = ns | 1;
             for (int i = lane; i < 2 * ns; i += 32) mw[i] = 0u;
             // ---- 1. distance block
-            if (kBF16) warp_gram_bf16(rows, geo.stride, nrm, D, ds, ns, m, st.dpb);
+            if (kKind == 2) warp_gram_fp8(rows, geo.stride, nrm, D, ds, ns, m, st.dpb);
+            else if (kKind == 1) warp_gram_bf16(rows, geo.stride, nrm, D, ds, ns, m, st.dpb);
             else warp_dist_f32(reinterpret_cast<const float4 *>(rows), geo.stride >> 4, st.nv, D, ds, ns, m);
             w_evals += (long long)m * (m - 1) / 2 + (long long)m * o;
             w_gathered += ns;
@@ -770,9 +825,9 @@ size_t set_kernel_smem(int cap) {
 }
 
 namespace {
-template <bool kBF16>
+template <int kKind>
 cudaError_t launch_ring_t(const DevState &st, int li, cudaStream_t s) {
-    auto kern = ring_join_kernel<kBF16>;
+    auto kern = ring_join_kernel<kKind>;
     constexpr uint32_t dyn = kRingBytes;
     cudaError_t e = smem_opt_in((const void *)kern, dyn);
     if (e != cudaSuccess) return e;
@@ -794,7 +849,8 @@ cudaError_t launch_set_kernel(const DevState &st, int li, cudaStream_t s) {
 cudaError_t launch_ring_join(const DevState &st, int li, cudaStream_t s) {
     cudaError_t e = st.u_lo == 0 ? launch_set_kernel(st, li, s) : cudaSuccess;
     if (e != cudaSuccess) return e;
-    return st.bf16 ? launch_ring_t<true>(st, li, s) : launch_ring_t<false>(st, li, s);
+    if (st.fp8) return launch_ring_t<2>(st, li, s);
+    return st.bf16 ? launch_ring_t<1>(st, li, s) : launch_ring_t<0>(st, li, s);
 }
 
 }  // namespace knng

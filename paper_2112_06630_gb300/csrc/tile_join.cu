@@ -22,6 +22,7 @@
 // dropped; one thread per target reserves a bucket run and writes its keys
 // from D; full buckets take the locked way.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cstdint>
@@ -430,6 +431,31 @@ __global__ void stage_bf16_kernel(const float *__restrict__ X, int64_t n, int dp
         acc = warp_sum(acc);
         if (lane == 0) nrm[u] = acc;
     }
+}
+
+__global__ void stage_fp8_kernel(const float *__restrict__ X, int64_t n, int dp, int d, uint8_t *__restrict__ X8,
+                                 int dpb, float *__restrict__ nrm) {
+    const unsigned lane = lane_id();
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n;
+         u += ((long long)gridDim.x * blockDim.x) >> 5) {
+        float acc = 0.f;
+        for (int t = lane; t < dpb; t += 32) {
+            const float v = t < d ? X[(size_t)u * dp + t] : 0.f;
+            const __nv_fp8_e4m3 b(v);  // round to nearest even, saturating
+            X8[(size_t)u * dpb + t] = b.__x;
+            const float f = (float)b;
+            acc = fmaf(f, f, acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) nrm[u] = acc;
+    }
+}
+
+cudaError_t launch_stage_fp8(const float *X, int64_t n, int dp, int d, uint8_t *X8, int dpb, float *nrm,
+                             cudaStream_t s) {
+    const int grid = grid_for((const void *)stage_fp8_kernel, 256, 0);
+    stage_fp8_kernel<<<grid, 256, 0, s>>>(X, n, dp, d, X8, dpb, nrm);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_stage_bf16(const float *X, int64_t n, int dp, int d, uint16_t *Xb, int dpb, float *nrm,
