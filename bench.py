@@ -247,8 +247,12 @@ def run_batched(args):
     mine = deal_by_cost([x.shape[0] * x.shape[1] for x in all_sets], ws)[rank]
     sets = [all_sets[i] for i in mine]
     xs = [torch.from_numpy(x).to(device) for x in sets]
-    flags = (knng.FLAG_BF16 if args.bf16 else 0) | (knng.FLAG_GRAPH if args.graph else 0) | \
-        (knng.FLAG_AUTOTUNE if args.autotune else 0)
+    # the batched form as built: each width class's loop one captured graph,
+    # its join kernel and block shape picked by the autotuner (--batched-plain
+    # switches both off)
+    tuned = not args.batched_plain
+    flags = (knng.FLAG_BF16 if args.bf16 else 0) | (knng.FLAG_GRAPH if (args.graph or tuned) else 0) | \
+        (knng.FLAG_AUTOTUNE if (args.autotune or tuned) else 0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     K, rho, delta, it = cfg["K"], cfg["rho"], cfg["delta"], cfg["max_iters"]
 
@@ -310,8 +314,8 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "bf16+f32" if args.bf16 else "f32", "data": "synthetic",
         "config": {"workload": "batched_256", "datasets": len(all_sets),
                    "total_n": int(sum(len(x) for x in all_sets)), "K": K, "rho": rho, "delta": delta,
-                   "max_iters": it, "bf16": bool(args.bf16), "graph": bool(args.graph),
-                   "autotune": bool(args.autotune),
+                   "max_iters": it, "bf16": bool(args.bf16), "graph": bool(args.graph or tuned),
+                   "autotune": bool(args.autotune or tuned),
                    "parallelism": f"data sets dealt over {ws} rank(s) by n*d (largest first, least-loaded rank)",
                    "l2": "flushed between timed steps (256 MiB write)", "inputs": "device-resident"},
         "e2e": {"value": round(ve, 6), "unit": "s", "h2d_bytes_per_step": int(sum(x.nbytes for x in sets)),
@@ -609,7 +613,7 @@ def _time_builds(knng, xd, op, flags, steps, warmup, flush, stream, ws=1, seed=0
 
 
 JOIN_KERNELS = {0: "join_kernel", 1: "tile_join_kernel", 2: "set_kernel+ring_join_kernel",
-                3: "set_kernel+pipe_join_kernel"}
+                3: "set_kernel+pipe_join_kernel", 4: "set_kernel+pipe_join_kernel<8,2>"}
 
 
 def run_gpu(args):
@@ -932,6 +936,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["batched_256"],
                     help="another workload than the headline one (measurement table)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
+    ap.add_argument("--batched-plain", action="store_true",
+                    help="batched workload without the captured graph and the autotuner")
     ap.add_argument("--sweep-d", action="store_true", help="dimension sweep at n=16,384 (one JSON line per run)")
     ap.add_argument("--bruteforce", action="store_true", help="time the exact brute-force K-NNG on the workload")
     ap.add_argument("--rows", type=int, default=0, help="brute force: sampled query rows (0 = every row)")

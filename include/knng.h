@@ -110,8 +110,9 @@ typedef struct knng_stats {
     int32_t join_ran;          /* timed iterations that ran (not skipped) */
     int32_t join_path;         /* local-join kernel: 0 warp per node (float32 rows of up to 32
                                   floats), 1 block-per-node tiles, 2 ring of nodes in flight
-                                  (bf16 rows), 3 pipelined block per node (float32 rows of 33
-                                  to 256 floats) */
+                                  (bf16 and FP8 rows), 3 pipelined block per node (float32 rows
+                                  of 33 to 256 floats; four warps, one row slot), 4 the same
+                                  with eight warps and two row slots */
     double join_ms_ran;        /* summed join-kernel time of those iterations (all passes) */
     double merge_ms_ran;       /* summed list-merge-kernel time of those iterations (all passes) */
     double sample_ms_ran;      /* summed selection-step time (degree count + sampling kernels) of

@@ -250,7 +250,7 @@ int ctx_alloc(knng_ctx *c) {
     const size_t oE = take(sizeof(int));
     const size_t oXb = c->fp8 ? take((size_t)n * c->dpb) : c->bf16 ? take(sizeof(uint16_t) * n * c->dpb) : 0;
     const size_t oXn = (c->bf16 || c->fp8) ? take(sizeof(float) * n) : 0;
-    const bool ring = c->join_path == kJoinRing || c->join_path == kJoinPipe ||
+    const bool ring = c->join_path == kJoinRing || c->join_path == kJoinPipe || c->join_path == kJoinPipe8 ||
                       (c->tune_pending && (ring_join_fits(c->kind(), c->nv, c->dpb, c->K) ||
                                            pipe_join_fits(c->kind(), c->nv)));
     const size_t oCs = ring ? take(sizeof(int) * (size_t)n * kSetMax) : 0;
@@ -395,6 +395,7 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
         else if (!std::strcmp(e, "tile")) force = kJoinTile;
         else if (!std::strcmp(e, "ring")) force = kJoinRing;
         else if (!std::strcmp(e, "pipe")) force = kJoinPipe;
+        else if (!std::strcmp(e, "pipe8")) force = kJoinPipe8;
     }
     c->join_path = choose_join_path(c->kind(), c->nv, c->dpb, K, force);
     if ((flags & KNNG_FLAG_AUTOTUNE) && force < 0) {
@@ -474,7 +475,10 @@ int autotune_join(knng_ctx *c, int li) {
     if (c->kind() < 2) paths.push_back(kJoinTile);
     if (c->kind() == 0) paths.push_back(kJoinWarp);
     if (ring_join_fits(c->kind(), c->nv, c->dpb, c->K) && c->cset) paths.push_back(kJoinRing);
-    if (pipe_join_fits(c->kind(), c->nv) && c->cset) paths.push_back(kJoinPipe);
+    if (pipe_join_fits(c->kind(), c->nv) && c->cset) {
+        paths.push_back(kJoinPipe);
+        paths.push_back(kJoinPipe8);
+    }
     const size_t kb = sizeof(uint64_t) * (size_t)c->n * c->K;
     unsigned char *tmp = nullptr;
     KNNG_TRY(lib_malloc((void **)&tmp, align256(kb) + sizeof(long long) * kStatCount, c->stream));

@@ -231,7 +231,9 @@ struct DevState {
 };
 
 // Which local-join kernel a context uses (fixed at creation).
-enum JoinPath : int { kJoinWarp = 0, kJoinTile = 1, kJoinRing = 2, kJoinPipe = 3 };
+// kJoinPipe: the pipelined kernel with four compute warps and one row slot per
+// block; kJoinPipe8: the same kernel with eight warps and two slots
+enum JoinPath : int { kJoinWarp = 0, kJoinTile = 1, kJoinRing = 2, kJoinPipe = 3, kJoinPipe8 = 4 };
 
 // Proposal buckets: run 0 of node p is inline (pbucket), runs 1..15 are pool
 // chunks claimed on demand with a CAS (a lane that loses the race uses the

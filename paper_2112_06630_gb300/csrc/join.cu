@@ -541,17 +541,17 @@ int choose_join_path(int bf16, int nv, int dpb, int K, int force) {
     if (force == kJoinWarp && !bf16) return kJoinWarp;
     if (force == kJoinTile) return kJoinTile;
     if (force == kJoinRing && ring) return kJoinRing;
-    if (force == kJoinPipe && pipe) return kJoinPipe;
+    if ((force == kJoinPipe || force == kJoinPipe8) && pipe) return force;
     if (!bf16 && nv <= kWarpMaxNv) return kJoinWarp;
     if (pipe) return kJoinPipe;
     return ring && ring_join_preferred(bf16, nv, dpb) ? kJoinRing : kJoinTile;
 }
 
-int join_launches(int path) { return path == kJoinRing || path == kJoinPipe ? 2 : 1; }
+int join_launches(int path) { return path == kJoinRing || path == kJoinPipe || path == kJoinPipe8 ? 2 : 1; }
 
 cudaError_t launch_join(const DevState &st, int li, cudaStream_t s) {
     if (st.join_path == kJoinRing) return launch_ring_join(st, li, s);
-    if (st.join_path == kJoinPipe) return launch_pipe_join(st, li, s);
+    if (st.join_path == kJoinPipe || st.join_path == kJoinPipe8) return launch_pipe_join(st, li, s);
     // high dimensions: block-per-node tiles (bf16 tensor cores when asked)
     if (st.join_path == kJoinTile) return launch_tile_join(st, li, st.bf16 != 0, s);
     const JoinLayout lay = join_layout(st.cap, st.nv, true);

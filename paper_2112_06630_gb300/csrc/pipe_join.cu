@@ -38,8 +38,6 @@
 // a wait that gives up raises the timeout counter and the block winds down
 // once the copies it issued have landed (again a bounded wait).
 #include <cstdint>
-#include <cstdlib>
-#include <cstring>
 
 #include "join_common.cuh"
 
@@ -516,14 +514,13 @@ cudaError_t launch_pipe_shape(const DevState &st, int li, cudaStream_t s) {
 cudaError_t launch_pipe_join(const DevState &st, int li, cudaStream_t s) {
     cudaError_t e = st.u_lo == 0 ? launch_set_kernel(st, li, s) : cudaSuccess;
     if (e != cudaSuccess) return e;
-    // four compute warps and one row slot per block, four blocks per SM:
-    // measured against eight warps with two slots (two blocks per SM) on the
-    // 1M x 128 mixture, join per launch 14.4 -> 10.2 ms at rho 0.3 and 29.4 ->
-    // 23.4 ms at rho 0.7, and 1.28 -> 0.71 ms on the 54k x 192 audio shape
-    // (more nodes in flight per SM beat deeper prefetch per block); a test
-    // hook selects the other shape
-    const char *shape = std::getenv("KNNG_TEST_PIPE_SHAPE");
-    if (shape && !std::strcmp(shape, "8x2")) return launch_pipe_shape<8, 2>(st, li, s);
+    // four compute warps and one row slot per block, four blocks per SM (the
+    // default): measured against eight warps with two slots (two blocks per
+    // SM) on the 1M x 128 mixture, join per launch 14.4 -> 10.2 ms at rho 0.3
+    // and 29.4 -> 23.4 ms at rho 0.7, and 1.28 -> 0.71 ms on the 54k x 192
+    // audio shape (more nodes in flight per SM beat deeper prefetch per
+    // block); the autotuner tries both
+    if (st.join_path == kJoinPipe8) return launch_pipe_shape<8, 2>(st, li, s);
     return launch_pipe_shape<4, 1>(st, li, s);
 }
 
