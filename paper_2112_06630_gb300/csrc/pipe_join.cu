@@ -16,12 +16,13 @@
 //     mbarrier, so the next node's rows land while the current one's
 //     proposals go out;
 //   compute warps (four, together on the current node):
-//     1. the distance block D[i][j] of the new rows i against all rows j, in
-//        the canonical float32 difference form (bit-identical to every other
-//        float32 distance of the library), register-blocked RB rows x 4
-//        columns per thread, RB chosen per node (2 or 1) so that small
-//        nodes still spread over the block; then the row slot is released
-//        to the producer;
+//     1. the distances the node's joins need, each pair once (new x new in
+//        2 x 2 register blocks over the upper triangle, new x old in 2 x 4
+//        blocks), or for small nodes the whole block of new rows against all
+//        rows in 1 x 4 items (more items to spread), whichever ends sooner on
+//        the slowest thread; canonical float32 difference form (bit-identical
+//        to every other float32 distance of the library) into D[i][j] for new
+//        i and every j; then the row slot is released to the producer;
 //     2. proposals, one warp per target: a new target takes partner j when
 //        key(D[t][j], j) orders before its snapshot worst entry, an old target
 //        takes new partner i when key(D[i][t], i) does -- every proposal of the
@@ -49,10 +50,7 @@ namespace {
 constexpr int kPipeMaxSlots = 2;
 template <int W, int S>
 struct PipeShape {
-    static constexpr int kWarps = W;
-    static constexpr int kCompute = 32 * W;
     static constexpr int kThreads = 32 * (W + 1);
-    static constexpr int kSlots = S;
     static constexpr int kMinBlocks = W == 8 ? 2 : 4;
 };
 constexpr int kPipeMaxUnits = 64;                   // 16-byte units per row: rows of up to 256 floats
@@ -154,63 +152,121 @@ __device__ __forceinline__ void cpa8(uint32_t dst, const void *src) {
 template <int NT>
 __device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
 
-// float4 unit v of row r in a slot's row area
-__device__ __forceinline__ const float4 *pipe_unit(const unsigned char *rows, const PipeGeo &g, int r, int v) {
-    const int cb = v >> 5;
-    return reinterpret_cast<const float4 *>(rows + g.off[cb] + (uint32_t)r * g.stride[cb] + (uint32_t)(v & 31) * 16u);
+// Canonical distances of the given rows (RB) against the given columns (CB)
+// of a slot, accumulated over every 16-byte unit in ascending order.
+template <int RB, int CB>
+__device__ __forceinline__ void pipe_block(const unsigned char *rows, const PipeGeo &g, const int (&ri)[RB],
+                                           const int (&cj)[CB], Acc4 (&acc)[RB][CB]) {
+    for (int cb = 0; cb < g.nblk; ++cb) {
+        const unsigned char *base = rows + g.off[cb];
+        const uint32_t st = g.stride[cb];
+        const int units = g.nv - 32 * cb < 32 ? g.nv - 32 * cb : 32;
+        const float4 *pr[RB], *pc[CB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) pr[r] = reinterpret_cast<const float4 *>(base + (uint32_t)ri[r] * st);
+#pragma unroll
+        for (int q = 0; q < CB; ++q) pc[q] = reinterpret_cast<const float4 *>(base + (uint32_t)cj[q] * st);
+        for (int v = 0; v < units; ++v) {
+            float4 x[RB], y[CB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) x[r] = pr[r][v];
+#pragma unroll
+            for (int q = 0; q < CB; ++q) y[q] = pc[q][v];
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+#pragma unroll
+                for (int q = 0; q < CB; ++q) acc[r][q].add(x[r], y[q]);
+        }
+    }
 }
 
-// Distance block of the new rows against all rows, RB rows x 4 columns per
-// item: rows a + r MA, columns b + q NB (consecutive threads take consecutive
-// b: consecutive rows, distinct banks; the RB rows are shared by a warp).
-template <int RB, int NT>
-__device__ __forceinline__ void pipe_dist(const unsigned char *rows, const PipeGeo &g, float *D, int ns, int m,
-                                          int tid) {
-    const int MA = (m + RB - 1) / RB, NB = (ns + 3) >> 2, items = MA * NB;
+// The whole block of the new rows against all rows, one row x 4 columns per
+// item (rows i, columns b + q NB): more, smaller items than pipe_dist_pairs,
+// which small nodes need to spread over the block.
+template <int NT>
+__device__ __forceinline__ void pipe_dist_rows(const unsigned char *rows, const PipeGeo &g, float *D, int ns, int m,
+                                               int tid) {
+    const int NB = (ns + 3) >> 2, items = m * NB;
     const uint32_t nbm = div_magic((uint32_t)NB);
     for (int e = tid; e < items; e += NT) {
-        const int a = (int)div_small((uint32_t)e, (uint32_t)NB, nbm), b = e - a * NB;
-        int ri[RB], cj[4];
-        bool vr[RB], vc[4];
-#pragma unroll
-        for (int r = 0; r < RB; ++r) {
-            ri[r] = a + r * MA;
-            vr[r] = ri[r] < m;
-            if (!vr[r]) ri[r] = a;
-        }
+        const int i = (int)div_small((uint32_t)e, (uint32_t)NB, nbm), b = e - i * NB;
+        int ri[1] = {i}, cj[4];
+        bool vc[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             cj[q] = b + q * NB;
             vc[q] = cj[q] < ns;
             if (!vc[q]) cj[q] = b;
         }
-        Acc4 acc[RB][4];
-        for (int cb = 0; cb < g.nblk; ++cb) {
-            const unsigned char *base = rows + g.off[cb];
-            const uint32_t st = g.stride[cb];
-            const int units = g.nv - 32 * cb < 32 ? g.nv - 32 * cb : 32;
-            const float4 *pr[RB], *pc[4];
+        Acc4 acc[1][4];
+        pipe_block<1, 4>(rows, g, ri, cj, acc);
 #pragma unroll
-            for (int r = 0; r < RB; ++r) pr[r] = reinterpret_cast<const float4 *>(base + (uint32_t)ri[r] * st);
+        for (int q = 0; q < 4; ++q)
+            if (vc[q]) D[i * kPipeDStride + cj[q]] = acc[0][q].sum();
+    }
+}
+
+// The distance block a node's joins need, each pair once: the new x new
+// pairs and the new x old pairs.  New x new: rows a, a + M against columns
+// b, b + M (M = ceil(m / 2)) for a <= b only, so every unordered pair of new
+// rows is computed once (the a == b items also give the diagonal, unused, and
+// both orders of one pair, equal bit for bit); each distance is written to
+// D[x][y] and D[y][x].  New x old: rows a, a + M against old columns
+// m + b + q NBo.  Consecutive threads take consecutive b (consecutive rows,
+// distinct banks); a warp shares the rows a, a + M (broadcast).
+template <int NT>
+__device__ __forceinline__ void pipe_dist_pairs(const unsigned char *rows, const PipeGeo &g, float *D, int ns,
+                                                int m, int tid) {
+    const int M = (m + 1) >> 1, o = ns - m;
+    const int n1 = M * (M + 1) / 2;
+    const int NBo = (o + 3) >> 2, n2 = M * NBo;
+    const uint32_t nbm = div_magic((uint32_t)(NBo > 0 ? NBo : 1));
+    for (int e = tid; e < n1 + n2; e += NT) {
+        if (e < n1) {
+            // row a of the upper triangle starts at a (2M - a + 1) / 2
+            int a = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) pc[q] = reinterpret_cast<const float4 *>(base + (uint32_t)cj[q] * st);
-            for (int v = 0; v < units; ++v) {
-                float4 x[RB], y[4];
-#pragma unroll
-                for (int r = 0; r < RB; ++r) x[r] = pr[r][v];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) y[q] = pc[q][v];
-#pragma unroll
-                for (int r = 0; r < RB; ++r)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[r][q].add(x[r], y[q]);
+            for (int step = 16; step > 0; step >>= 1) {
+                const int c = a + step;
+                if (c < M && c * (2 * M - c + 1) / 2 <= e) a = c;
             }
+            const int b = a + (e - a * (2 * M - a + 1) / 2);
+            int ri[2] = {a, a + M}, cj[2] = {b, b + M};
+            const bool vr1 = ri[1] < m, vc1 = cj[1] < m;
+            if (!vr1) ri[1] = a;
+            if (!vc1) cj[1] = b;
+            Acc4 acc[2][2];
+            pipe_block<2, 2>(rows, g, ri, cj, acc);
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    if ((r && !vr1) || (q && !vc1)) continue;
+                    const float dd = acc[r][q].sum();
+                    D[ri[r] * kPipeDStride + cj[q]] = dd;
+                    D[cj[q] * kPipeDStride + ri[r]] = dd;
+                }
+        } else {
+            const int e2 = e - n1;
+            const int a = (int)div_small((uint32_t)e2, (uint32_t)NBo, nbm), b = e2 - a * NBo;
+            int ri[2] = {a, a + M}, cj[4];
+            bool vc[4];
+            const bool vr1 = ri[1] < m;
+            if (!vr1) ri[1] = a;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cj[q] = m + b + q * NBo;
+                vc[q] = cj[q] < ns;
+                if (!vc[q]) cj[q] = m + b;
+            }
+            Acc4 acc[2][4];
+            pipe_block<2, 4>(rows, g, ri, cj, acc);
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if ((r == 0 || vr1) && vc[q]) D[ri[r] * kPipeDStride + cj[q]] = acc[r][q].sum();
         }
-#pragma unroll
-        for (int r = 0; r < RB; ++r)
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (vr[r] && vc[q]) D[ri[r] * kPipeDStride + cj[q]] = acc[r][q].sum();
     }
 }
 }  // namespace
@@ -342,13 +398,16 @@ __global__ void __launch_bounds__(PipeShape<W, S>::kThreads, PipeShape<W, S>::kM
             }
             // ---- 1. distance block (RB so that the items fill the block)
             const unsigned char *rows = sb + kPipeHdrBytes;
-            const int nb = (ns + 3) >> 2;
-            // 2 x 4 items unless 1 x 4 items finish sooner: the slowest thread
-            // takes ceil(items / threads) items (the others wait at the barrier)
-            const int waves2 = (((m + 1) >> 1) * nb + kPipeCompute - 1) / kPipeCompute;
-            const int waves1 = (m * nb + kPipeCompute - 1) / kPipeCompute;
-            if (8 * waves2 <= 5 * waves1) pipe_dist<2, kPipeCompute>(rows, geo, cur->D, ns, m, tid);
-            else pipe_dist<1, kPipeCompute>(rows, geo, cur->D, ns, m, tid);
+            // each pair once in larger items, unless they would keep fewer than
+            // half the threads busy: then the whole block in 1 x 4 items, which
+            // spread a small node over more threads (measured on the 1M x 128
+            // mixture against pairs only: rho 0.3 join 12.1 -> 10.3 ms per
+            // iteration; rho 0.7, where most nodes are large, 17.9 -> 17.1 ms)
+            {
+                const int M = (m + 1) >> 1, items_p = M * (M + 1) / 2 + M * ((ns - m + 3) >> 2);
+                if (2 * items_p >= kPipeCompute) pipe_dist_pairs<kPipeCompute>(rows, geo, cur->D, ns, m, tid);
+                else pipe_dist_rows<kPipeCompute>(rows, geo, cur->D, ns, m, tid);
+            }
             compute_sync<kPipeCompute>();
             if (tid == 0) bar_arrive(&sh->empty[slot]);  // the rows are no longer read
             if (tid == 0) {
