@@ -17,6 +17,41 @@ constexpr int kBlock = kWarpsPerBlock * 32;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 __device__ __forceinline__ long long gwarp() { return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+
+// Rows gathered whole into shared memory before the distances of a list:
+// blocks of four warps, each warp with 33 rows on a stride of (nv | 1)
+// 16-byte units (consecutive rows on distinct banks); taken for rows of up to
+// kStageMinNv to kStageMaxNv units.  A lane reading its own row 16 bytes at a time from
+// global memory used half of each sector it fetched.
+constexpr int kStageWarps = 4;
+constexpr int kStageMinNv = 16;  // shorter rows are a sector or two: read directly
+constexpr int kStageMaxNv = 90;
+__host__ __device__ __forceinline__ size_t stage_smem_bytes(int nv) {
+    return (size_t)kStageWarps * 33 * (size_t)(nv | 1) * 16;
+}
+__device__ __forceinline__ void cp_async16_n(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+// Lane k (< cnt) gets the canonical distance between row u and row v_k (v
+// held by lane k); the rows are first copied whole into the warp's area sm
+// with asynchronous 16-byte copies (one warp instruction per 512 bytes).
+__device__ __forceinline__ float warp_staged_dist(const float4 *__restrict__ X4, int nv, long long u, uint32_t v,
+                                                  int cnt, float4 *sm) {
+    const unsigned lane = lane_id();
+    const int rs = nv | 1;
+    float4 *own = sm + 32 * rs;
+    for (int k = 0; k < cnt; ++k) {
+        const uint32_t vk = __shfl_sync(0xFFFFFFFFu, v, k);
+        for (int c = lane; c < nv; c += 32) cp_async16_n(sm + k * rs + c, X4 + (size_t)vk * nv + c);
+    }
+    for (int c = lane; c < nv; c += 32) cp_async16_n(own + c, X4 + (size_t)u * nv + c);
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    const float dd = (int)lane < cnt ? l2sq_rows(own, sm + lane * rs, nv) : 0.f;
+    __syncwarp();
+    return dd;
+}
 __device__ __forceinline__ long long nwarps() { return ((long long)gridDim.x * blockDim.x) >> 5; }
 }  // namespace
 
@@ -123,8 +158,10 @@ cudaError_t prepare_stage() {
 // taken in order and a proposal is accepted unless it is u or already chosen.
 // A warp evaluates 32 consecutive attempts at once and accepts, in lane order,
 // exactly the proposals the sequential rule would accept.
+template <bool kStaged>
 __global__ void __launch_bounds__(kBlock) init_random_kernel(DevState st, uint64_t base, int *err) {
     __shared__ uint32_t chosen_s[kWarpsPerBlock][kMaxK];
+    extern __shared__ __align__(16) float4 stage_sm[];
     uint32_t *chosen = chosen_s[threadIdx.x >> 5];
     const unsigned lane = lane_id();
     const int K = st.K;
@@ -162,11 +199,11 @@ __global__ void __launch_bounds__(kBlock) init_random_kernel(DevState st, uint64
             }
         }
         uint64_t key = kKeyEmpty;
-        if ((int)lane < K) {
-            uint32_t v = chosen[lane];
-            float dd = l2sq_rows(X4 + (size_t)u * st.nv, X4 + (size_t)v * st.nv, st.nv);
-            key = make_key(dd, v, kFlagNew);
-        }
+        const uint32_t v = (int)lane < K ? chosen[lane] : (uint32_t)u;
+        float dd;
+        if (kStaged) dd = warp_staged_dist(X4, st.nv, u, v, K, stage_sm + (threadIdx.x >> 5) * 33 * (st.nv | 1));
+        else dd = (int)lane < K ? l2sq_rows(X4 + (size_t)u * st.nv, X4 + (size_t)v * st.nv, st.nv) : 0.f;
+        if ((int)lane < K) key = make_key(dd, v, kFlagNew);
         key = warp_sort_u64(key);
         if ((int)lane < K) st.keys[(size_t)u * K + lane] = key;
         __syncwarp();
@@ -174,8 +211,17 @@ __global__ void __launch_bounds__(kBlock) init_random_kernel(DevState st, uint64
 }
 
 cudaError_t launch_init_random(const DevState &st, uint64_t seed, int *err, cudaStream_t s) {
-    int grid = grid_for((const void *)init_random_kernel, kBlock, 0);
-    init_random_kernel<<<grid, kBlock, 0, s>>>(st, hash_base(seed, kStreamInit, 0), err);
+    const uint64_t base = hash_base(seed, kStreamInit, 0);
+    if (st.nv >= kStageMinNv && st.nv <= kStageMaxNv) {
+        const size_t dyn = stage_smem_bytes(st.nv);
+        cudaError_t e = smem_opt_in((const void *)init_random_kernel<true>, dyn);
+        if (e != cudaSuccess) return e;
+        const int grid = grid_for((const void *)init_random_kernel<true>, kStageWarps * 32, dyn);
+        init_random_kernel<true><<<grid, kStageWarps * 32, dyn, s>>>(st, base, err);
+        return cudaGetLastError();
+    }
+    int grid = grid_for((const void *)init_random_kernel<false>, kBlock, 0);
+    init_random_kernel<false><<<grid, kBlock, 0, s>>>(st, base, err);
     return cudaGetLastError();
 }
 
@@ -583,18 +629,22 @@ cudaError_t launch_invert(const int32_t *perm, int64_t n, int32_t *inv, cudaStre
 // total_perm[u]; every entry's distance is recomputed with the canonical
 // float32 difference form, ids are renamed back, and the row is re-sorted by
 // (dist, original id).
+template <bool kStaged>
 __global__ void __launch_bounds__(kBlock) output_kernel(DevState st, const int32_t *__restrict__ total_perm,
                                                         const int32_t *__restrict__ total_inv,
                                                         int32_t *__restrict__ ids, float *__restrict__ dists) {
+    extern __shared__ __align__(16) float4 stage_sm[];
     const unsigned lane = lane_id();
     const int K = st.K;
     const float4 *X4 = reinterpret_cast<const float4 *>(st.X);
     for (long long u = gwarp(); u < st.n; u += nwarps()) {
         const int64_t p = total_perm ? total_perm[u] : u;
         uint64_t key = kKeyEmpty;
+        const uint32_t v = (int)lane < K ? key_id(st.keys[(size_t)p * K + lane]) : (uint32_t)p;
+        float dd;
+        if (kStaged) dd = warp_staged_dist(X4, st.nv, p, v, K, stage_sm + (threadIdx.x >> 5) * 33 * (st.nv | 1));
+        else dd = (int)lane < K ? l2sq_rows(X4 + (size_t)p * st.nv, X4 + (size_t)v * st.nv, st.nv) : 0.f;
         if ((int)lane < K) {
-            uint32_t v = key_id(st.keys[(size_t)p * K + lane]);
-            float dd = l2sq_rows(X4 + (size_t)p * st.nv, X4 + (size_t)v * st.nv, st.nv);
             uint32_t vo = total_inv ? (uint32_t)total_inv[v] : v;
             if (st.ds) vo -= (uint32_t)st.ds_off[st.ds[u]];  // batched: ids local to the data set
             key = make_key(dd, vo, 0);
@@ -609,8 +659,16 @@ __global__ void __launch_bounds__(kBlock) output_kernel(DevState st, const int32
 
 cudaError_t launch_output(const DevState &st, const int32_t *total_perm, const int32_t *total_inv,
                           int32_t *ids, float *dists, cudaStream_t s) {
-    int grid = grid_for((const void *)output_kernel, kBlock, 0);
-    output_kernel<<<grid, kBlock, 0, s>>>(st, total_perm, total_inv, ids, dists);
+    if (st.nv >= kStageMinNv && st.nv <= kStageMaxNv) {
+        const size_t dyn = stage_smem_bytes(st.nv);
+        cudaError_t e = smem_opt_in((const void *)output_kernel<true>, dyn);
+        if (e != cudaSuccess) return e;
+        const int grid = grid_for((const void *)output_kernel<true>, kStageWarps * 32, dyn);
+        output_kernel<true><<<grid, kStageWarps * 32, dyn, s>>>(st, total_perm, total_inv, ids, dists);
+        return cudaGetLastError();
+    }
+    int grid = grid_for((const void *)output_kernel<false>, kBlock, 0);
+    output_kernel<false><<<grid, kBlock, 0, s>>>(st, total_perm, total_inv, ids, dists);
     return cudaGetLastError();
 }
 

@@ -772,6 +772,8 @@ def test_pipelined_join_block_shapes_match_oracle_bit_exact(shape, n, d, K, rho,
     assert ch == r["changes"]
 
 
+@pytest.mark.parametrize("n,d,K,rho,bf16", [(900, 1600, 16, 0.5, False), (900, 2000, 16, 0.5, True),
+                                            (700, 3144, 12, 0.5, False)])
 def test_wide_rows_match_oracle_bit_exact(n, d, K, rho, bf16):
     """Row widths the dimension sweep times (up to the paper's d = 3144),
     beyond the ring and pipelined kernels: the block-per-node tile kernel in
