@@ -771,6 +771,11 @@ def run_gpu(args):
         "iterations": stats["iterations"], "dist_evals": stats["dist_evals"],
         "candidates_over_cap": stats["set_overflow"],
         "selection_ms_per_iter": round(tst["sample_ms_ran"] / ran, 4),
+        # the proposal pipeline of the timed point: keys the joins handed to
+        # the list merges, and the list insertions they made
+        "proposals": {"keys": tst["proposals"], "insertions": tst["inserts"],
+                      "keys_per_insertion": round(tst["proposals"] / max(1, tst["inserts"]), 2),
+                      "merge_ms_per_iter": round(tst["merge_ms_ran"] / ran, 4)},
         "dist_evals_per_s": round(stats["dist_evals"] / step_s, 1),
         "paper_flops_per_s": round(stats["dist_evals"] * (3 * w.d - 1) / step_s, 1),
         "e2e": {"value": round(e2e_s, 6), "unit": "s", "h2d_bytes_per_step": int(x.nbytes),
