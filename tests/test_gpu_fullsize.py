@@ -136,7 +136,9 @@ def test_mixture_n1m_d128_full_size_vs_stored_oracle(case, rho, delta, iters):
 
 def test_batched_workload_slice_equals_single_builds():
     """32 data sets of the batched workload (every row-width class of it):
-    the batched build equals each data set's own build bit for bit."""
+    the batched build equals each data set's own build bit for bit, and on
+    the largest data set of each width its recall is the oracle's within the
+    parity tolerance."""
     specs = workloads.batched_specs(256, 0)[:32]
     sets = [workloads.gaussian_mixture(s["n"], s["d"], s["clusters"], seed=s["seed"]) for s in specs]
     xs = [torch.from_numpy(x).cuda() for x in sets]
@@ -146,6 +148,17 @@ def test_batched_workload_slice_equals_single_builds():
     for x, (bi, bd) in zip(xs, outs):
         si, sd, _ = knng.knng_build(x, cfg["K"], cfg["rho"], cfg["delta"], cfg["max_iters"], seed=0)
         assert torch.equal(bi, si) and torch.equal(bd, sd)
+    # and against the oracle: the largest data set of each row width, recall
+    # within the parity tolerance of the oracle's build at the same parameters
+    for d in sorted({s["d"] for s in specs}):
+        b = max((i for i, s in enumerate(specs) if s["d"] == d), key=lambda i: specs[i]["n"])
+        x = sets[b]
+        rows = np.random.default_rng(b).choice(len(x), min(1000, len(x)), replace=False)
+        exact = _ground_truth(x, xs[b], cfg["K"], rows)
+        oi, _, _ = oracle.build_knng_mt(x, cfg["K"], cfg["rho"], cfg["delta"], cfg["max_iters"], seed=0)
+        r_gpu = metrics.recall(x, outs[b][0].cpu().numpy(), exact, rows)
+        r_orc = metrics.recall(x, oi, exact, rows)
+        assert abs(r_gpu - r_orc) <= PARITY, (d, r_gpu, r_orc)
 
 
 def test_audio_like_relabelled_build_keeps_recall():
