@@ -56,15 +56,46 @@ __device__ __forceinline__ bool warp_insert(uint64_t &Lk, uint64_t x, int K) {
     return true;
 }
 
+// Reverse part raw[b, b + cnt) (cnt <= 96; reverse capacities are at most
+// 2 * 32 + 8) put in a fixed order: ascending by (id - base) * 0x9E3779B1 mod
+// 2^32, a bijection of the ids local to the data set (base: its first node),
+// so the order is canonical, the same in a batched build, and not tied to id
+// size.  The ids of one reverse part are distinct (a node lists an id once).
+__device__ __forceinline__ void warp_order_part(int *raw, int b, int cnt, uint32_t base) {
+    const unsigned lane = lane_id();
+    int v[3], r[3];
+    uint32_t k[3];
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {
+        const int i = (int)lane + 32 * h;
+        v[h] = i < cnt ? raw[b + i] : 0;
+        k[h] = ((uint32_t)v[h] - base) * 0x9E3779B1u;
+        r[h] = 0;
+    }
+    for (int j = 0; j < cnt; ++j) {
+        const uint32_t kj = ((uint32_t)raw[b + j] - base) * 0x9E3779B1u;
+#pragma unroll
+        for (int h = 0; h < 3; ++h) r[h] += kj < k[h];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 3; ++h)
+        if ((int)lane + 32 * h < cnt) raw[b + r[h]] = v[h];
+    __syncwarp();
+}
+
 // Node u's sampled candidates (one warp): the forward part written by u's
 // sampling warp and the reverse part filled by other warps, repeats removed
 // with a shared-memory hash set (new entries first, so an id that is both new
-// and old stays new; of repeats of one kind the copy whose insertion wins
-// stays, the set does not depend on which).  Writes sid[0 .. ns), new ones
-// first (m of them), capped at kSetMax.  raw must hold 2 * cap ints and hset
-// 2^kHashBits ints.  Lane 0 also restarts u's reverse degrees for the next
-// iteration.  Returns total raw ids read; ns = 0 when u has no new candidate
-// (no join pair).  Results are warp-uniform.
+// and old stays new; of repeats the first in read order stays).  Writes
+// sid[0 .. ns), new ones first (m of them), capped at kSetMax.  When the ids
+// read exceed the cap, each reverse part is first put in the fixed order of
+// warp_order_part: the forward parts are in list order already, so which ids
+// the cap drops does not depend on the order in which other warps took the
+// reverse slots, and the build stays deterministic.  raw must hold 2 * cap
+// ints and hset 2^kHashBits ints.  Lane 0 also restarts u's reverse degrees
+// for the next iteration.  Returns total raw ids read; ns = 0 when u has no
+// new candidate (no join pair).  Results are warp-uniform.
 __device__ __forceinline__ int warp_gather_candidates(const DevState &st, long long u, int *raw, int *hset, int *sid,
                                                       int &ns_out, int &m_out, long long &setovf) {
     const unsigned lane = lane_id();
@@ -92,15 +123,21 @@ __device__ __forceinline__ int warp_gather_candidates(const DevState &st, long l
     }
     for (int i = lane; i < (1 << kHashBits); i += 32) hset[i] = -1;
     __syncwarp();
+    if (total > kSetMax) {
+        const uint32_t base = (uint32_t)(u - node_local(st, u));
+        warp_order_part(raw, fn, rn, base);
+        warp_order_part(raw, nnew_raw + fo, ro, base);
+    }
     int ns = 0, m = 0;
     for (int pass = 0; pass < 2; ++pass) {
         const int lo_i = pass ? nnew_raw : 0, hi_i = pass ? total : nnew_raw;
         for (int b0 = lo_i; b0 < hi_i; b0 += 32) {
             const int idx = b0 + lane;
             bool keep = false;
-            int v = -1;
-            if (idx < hi_i) {
-                v = raw[idx];
+            const int v = idx < hi_i ? raw[idx] : -1;
+            // of repeats within the batch only the lowest lane competes
+            const unsigned grp = __match_any_sync(kFull, v);
+            if (idx < hi_i && (grp & lanemask_lt()) == 0) {
                 unsigned h = ((unsigned)v * 0x9E3779B1u) >> (32 - kHashBits);
                 for (int probe = 0; probe < (1 << kHashBits); ++probe) {
                     const int prev = atomicCAS(hset + h, -1, v);

@@ -249,6 +249,34 @@ def test_join_kernels_agree_on_real_valued_builds(path, monkeypatch):
     assert torch.equal(ids, ids_w) and torch.equal(dists, dists_w)
 
 
+@pytest.mark.parametrize("d", [24, 72])
+def test_capped_candidate_sets_are_deterministic(d, monkeypatch):
+    """K = 32 at rho 1.0: a node's sampled union (forward up to K, reverse
+    new and old up to s each) passes the cap of 64 candidates on many nodes,
+    and the cap drops the tail of a canonical order (reverse parts ordered by
+    a fixed bijection of the ids, first copy of a repeat kept).  So the graph
+    does not depend on the order in which other warps took the reverse slots:
+    repeated builds, every join kernel and a batched build (other data sets
+    interleaved in the same launches) give the same graph bit for bit."""
+    x = workloads.gaussian_mixture(4000, d, 12, seed=d)
+    xd = _cuda(x)
+    ref_i, ref_d, st = knng.knng_build(xd, 32, 1.0, 0.001, 6, seed=3)
+    assert st["set_overflow"] > 0 and st["lock_timeouts"] == 0
+    for _ in range(2):
+        ids, dists, _ = knng.knng_build(xd, 32, 1.0, 0.001, 6, seed=3)
+        assert torch.equal(ids, ref_i) and torch.equal(dists, ref_d)
+    for path in ("warp", "tile", "ring", "pipe") if d > 32 else ("warp", "tile", "ring"):
+        monkeypatch.setenv("KNNG_TEST_JOIN_PATH", path)
+        ids, dists, st_p = knng.knng_build(xd, 32, 1.0, 0.001, 6, seed=3)
+        assert st_p["join_path"] == PATH_IDS[path]
+        assert torch.equal(ids, ref_i) and torch.equal(dists, ref_d), path
+    monkeypatch.delenv("KNNG_TEST_JOIN_PATH")
+    others = [workloads.gaussian_mixture(3000 + 500 * b, d, 10, seed=100 + b) for b in range(3)]
+    outs, _ = knng.knng_build_batched([_cuda(o) for o in others[:2]] + [xd] + [_cuda(others[2])], 32, 1.0,
+                                      0.001, 6, seed=3)
+    assert torch.equal(outs[2][0], ref_i) and torch.equal(outs[2][1], ref_d)
+
+
 @pytest.mark.parametrize("pool", ["1", "40"])
 def test_bucket_overflow_paths_match_oracle_bit_exact(pool, monkeypatch):
     """A (test-only) tiny proposal pool forces runs past the first 256 keys of
