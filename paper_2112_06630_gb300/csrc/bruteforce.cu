@@ -27,7 +27,7 @@ constexpr int kBfSmem = 64 * 1024;
 // own row in registers (NVR float4) when nv <= NVR; same operation order as l2sq_rows
 template <int NVR>
 __device__ __forceinline__ float l2sq_reg(const float4 (&a)[NVR], const float4 *__restrict__ b) {
-    Acc4 acc;
+    Acc2 acc;
 #pragma unroll
     for (int v = 0; v < NVR; ++v) acc.add(a[v], b[v]);
     return acc.sum();

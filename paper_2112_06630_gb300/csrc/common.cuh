@@ -59,15 +59,17 @@ __device__ __forceinline__ bool accept(uint64_t h, uint32_t cnt, uint32_t s) {
 
 // ----------------------------------------------------------- distance ----
 // Canonical float32 squared l2 (difference form, no square root): rows are
-// zero-padded to a multiple of 4 floats; four partial sums over t mod 4, each
-// accumulated in ascending t with fused multiply-add, combined as
-// (s0 + s1) + (s2 + s3).  Every float32 distance in the library (init, join,
-// brute force, re-rank) uses exactly this order, so one pair always gets one
-// value and the two orders of a pair agree bit for bit.
-// The partial sums run as two packed pairs (s0, s1) and (s2, s3) on the
-// paired float32 instructions of sm_100+ (sub.rn.f32x2, fma.rn.f32x2): each
-// lane of a pair is the IEEE round-to-nearest operation of the scalar form,
-// so the values are those of four scalar chains, with half the instructions.
+// zero-padded to a multiple of 4 floats; two partial sums over t mod 2, each
+// accumulated in ascending t with fused multiply-add, combined as s0 + s1.
+// Every float32 distance in the library (init, join, brute force, re-rank)
+// uses exactly this order, so one pair always gets one value and the two
+// orders of a pair agree bit for bit.
+// The partial sums run as one packed pair (s0, s1) on the paired float32
+// instructions of sm_100+ (sub.rn.f32x2, fma.rn.f32x2): each lane of the pair
+// is the IEEE round-to-nearest operation of the scalar form, so the values are
+// those of two scalar chains, with half the instructions.  Two sums (not
+// four) keep a pair's accumulator in one 64-bit register, which leaves the
+// register-blocked join kernels room to load the next unit ahead.
 __device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi) {
     unsigned long long r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
@@ -76,26 +78,25 @@ __device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi) {
 __device__ __forceinline__ void f32x2_unpack(unsigned long long v, float &lo, float &hi) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
-struct Acc4 {
-    unsigned long long s01, s23;  // (s0, s1), (s2, s3)
-    __device__ __forceinline__ Acc4() : s01(0ull), s23(0ull) {}
+struct Acc2 {
+    unsigned long long s;  // (s0, s1): the elements t even and t odd
+    __device__ __forceinline__ Acc2() : s(0ull) {}
     __device__ __forceinline__ void add(float4 a, float4 b) {
         unsigned long long d01, d23;
         asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d01) : "l"(f32x2_pack(a.x, a.y)), "l"(f32x2_pack(b.x, b.y)));
         asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d23) : "l"(f32x2_pack(a.z, a.w)), "l"(f32x2_pack(b.z, b.w)));
-        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(s01) : "l"(d01));
-        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(s23) : "l"(d23));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(s) : "l"(d01));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(s) : "l"(d23));
     }
     __device__ __forceinline__ float sum() const {
-        float s0, s1, s2, s3;
-        f32x2_unpack(s01, s0, s1);
-        f32x2_unpack(s23, s2, s3);
-        return (s0 + s1) + (s2 + s3);
+        float s0, s1;
+        f32x2_unpack(s, s0, s1);
+        return s0 + s1;
     }
 };
 
 __device__ __forceinline__ float l2sq_rows(const float4 *__restrict__ a, const float4 *__restrict__ b, int nv) {
-    Acc4 acc;
+    Acc2 acc;
     for (int v = 0; v < nv; ++v) acc.add(a[v], b[v]);
     return acc.sum();
 }

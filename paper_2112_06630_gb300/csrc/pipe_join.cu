@@ -156,7 +156,7 @@ __device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, %0;" 
 // of a slot, accumulated over every 16-byte unit in ascending order.
 template <int RB, int CB>
 __device__ __forceinline__ void pipe_block(const unsigned char *rows, const PipeGeo &g, const int (&ri)[RB],
-                                           const int (&cj)[CB], Acc4 (&acc)[RB][CB]) {
+                                           const int (&cj)[CB], Acc2 (&acc)[RB][CB]) {
     for (int cb = 0; cb < g.nblk; ++cb) {
         const unsigned char *base = rows + g.off[cb];
         const uint32_t st = g.stride[cb];
@@ -198,7 +198,7 @@ __device__ __forceinline__ void pipe_dist_rows(const unsigned char *rows, const 
             vc[q] = cj[q] < ns;
             if (!vc[q]) cj[q] = b;
         }
-        Acc4 acc[1][4];
+        Acc2 acc[1][4];
         pipe_block<1, 4>(rows, g, ri, cj, acc);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -235,7 +235,7 @@ __device__ __forceinline__ void pipe_dist_pairs(const unsigned char *rows, const
             const bool vr1 = ri[1] < m, vc1 = cj[1] < m;
             if (!vr1) ri[1] = a;
             if (!vc1) cj[1] = b;
-            Acc4 acc[2][2];
+            Acc2 acc[2][2];
             pipe_block<2, 2>(rows, g, ri, cj, acc);
 #pragma unroll
             for (int r = 0; r < 2; ++r)
@@ -259,7 +259,7 @@ __device__ __forceinline__ void pipe_dist_pairs(const unsigned char *rows, const
                 vc[q] = cj[q] < ns;
                 if (!vc[q]) cj[q] = m + b;
             }
-            Acc4 acc[2][4];
+            Acc2 acc[2][4];
             pipe_block<2, 4>(rows, g, ri, cj, acc);
 #pragma unroll
             for (int r = 0; r < 2; ++r)

@@ -228,7 +228,7 @@ __device__ __forceinline__ void warp_dist_f32(const float4 *rows, uint32_t rs, i
             vc[q] = j < ns;
             c[q] = rows + (size_t)(vc[q] ? j : b) * rs;
         }
-        Acc4 acc0[4], acc1[4];
+        Acc2 acc0[4], acc1[4];
         for (int v = 0; v < nv; ++v) {
             const float4 x0 = r0[v], x1 = r1[v];
 #pragma unroll

@@ -7,7 +7,7 @@
 // floats, or 64 bf16), double-buffered with cp.async.
 //   - float32: one item = one new row and four columns, spread evenly over
 //     the block (only the pairs the node needs), accumulating the canonical
-//     difference form (four partial sums over t mod 4, ascending t, fused
+//     difference form (two partial sums over t mod 2, ascending t, fused
 //     multiply-add), so every value is bit-identical to the warp kernel and to
 //     the rest of the library.  Rows are read by broadcast (i) and by 8-thread
 //     phases on an odd float4 stride (j): no bank conflicts.
@@ -98,7 +98,7 @@ __device__ void tile_dist_f32(TileSmem &sm, float4 *stage, const float4 *X4, int
     const int nchunks = (nv + kChunkV - 1) / kChunkV;
     float4 *buf[2] = {stage, stage + kSetMax * kStrideV};
     for (int it0 = 0; it0 < items; it0 += kTileThreads * kItemsPerThread) {
-        Acc4 acc[kItemsPerThread][4];
+        Acc2 acc[kItemsPerThread][4];
         int ii[kItemsPerThread], jj[kItemsPerThread];
 #pragma unroll
         for (int w = 0; w < kItemsPerThread; ++w) {
