@@ -626,9 +626,11 @@ cudaError_t launch_invert(const int32_t *perm, int64_t n, int32_t *inv, cudaStre
 
 // ------------------------------------------------------ re-rank + output ----
 // Final lists in the caller's labelling: original node u's list lives at spot
-// total_perm[u]; every entry's distance is recomputed with the canonical
-// float32 difference form, ids are renamed back, and the row is re-sorted by
-// (dist, original id).
+// total_perm[u]; ids are renamed back and the row is re-sorted by (dist,
+// original id).  Float32 keys already hold the canonical float32 distance of
+// their pair (init and every join compute it the same way, and both orders of
+// a pair agree bit for bit), so they are taken as they are; the approximate
+// keys of the bf16 and FP8 forms are re-ranked with the canonical distance.
 template <bool kStaged>
 __global__ void __launch_bounds__(kBlock) output_kernel(DevState st, const int32_t *__restrict__ total_perm,
                                                         const int32_t *__restrict__ total_inv,
@@ -640,9 +642,11 @@ __global__ void __launch_bounds__(kBlock) output_kernel(DevState st, const int32
     for (long long u = gwarp(); u < st.n; u += nwarps()) {
         const int64_t p = total_perm ? total_perm[u] : u;
         uint64_t key = kKeyEmpty;
-        const uint32_t v = (int)lane < K ? key_id(st.keys[(size_t)p * K + lane]) : (uint32_t)p;
+        const uint64_t lk = (int)lane < K ? st.keys[(size_t)p * K + lane] : kKeyEmpty;
+        const uint32_t v = (int)lane < K ? key_id(lk) : (uint32_t)p;
         float dd;
-        if (kStaged) dd = warp_staged_dist(X4, st.nv, p, v, K, stage_sm + (threadIdx.x >> 5) * 33 * (st.nv | 1));
+        if (!st.bf16) dd = (int)lane < K ? key_dist(lk) : 0.f;
+        else if (kStaged) dd = warp_staged_dist(X4, st.nv, p, v, K, stage_sm + (threadIdx.x >> 5) * 33 * (st.nv | 1));
         else dd = (int)lane < K ? l2sq_rows(X4 + (size_t)p * st.nv, X4 + (size_t)v * st.nv, st.nv) : 0.f;
         if ((int)lane < K) {
             uint32_t vo = total_inv ? (uint32_t)total_inv[v] : v;
@@ -659,7 +663,7 @@ __global__ void __launch_bounds__(kBlock) output_kernel(DevState st, const int32
 
 cudaError_t launch_output(const DevState &st, const int32_t *total_perm, const int32_t *total_inv,
                           int32_t *ids, float *dists, cudaStream_t s) {
-    if (st.nv >= kStageMinNv && st.nv <= kStageMaxNv) {
+    if (st.bf16 && st.nv >= kStageMinNv && st.nv <= kStageMaxNv) {
         const size_t dyn = stage_smem_bytes(st.nv);
         cudaError_t e = smem_opt_in((const void *)output_kernel<true>, dyn);
         if (e != cudaSuccess) return e;
