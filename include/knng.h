@@ -143,7 +143,12 @@ int knng_build_ex(const float *data, int64_t n, int d, int K, float rho, float d
 /*
  * Create a context and run the random initialisation (Section 2: K distinct
  * neighbours != u per point, uniform over V).  Allocates all device memory
- * the build needs.  *out is NULL on error.
+ * the build needs: the padded points, lists, candidate arrays and proposal
+ * buckets take about 2.5 KiB + 4 (d rounded up to 4) + 16 K + 16 s bytes per
+ * point (s = ceil(rho K)), plus a bucket pool of 4 KiB per point up to
+ * 16 GiB (at d = 128, K = 32, rho 0.7: 7.8 KiB per point up to 4M points,
+ * then 3.8 KiB per point plus 16 GiB; past 4M points an iteration runs in
+ * more node-range passes instead).  *out is NULL on error.
  */
 int knng_init(knng_ctx **out, const float *data, int64_t n, int d, int K, float rho,
               float delta, uint64_t seed, uint32_t flags, void *stream);

@@ -365,8 +365,12 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
     c->R = rev_capacity(c->s);
     c->cap = K + c->R;
     // bucket pool: two 256-key runs per node on top of the inline run (the
-    // first, dense iteration averages about (2s)^2 proposals per node)
-    c->pool_chunks = (int)std::min<int64_t>(2 * n + 4096, (int64_t)1 << 30);
+    // first, dense iteration averages about (2s)^2 proposals per node), but at
+    // most 16 GiB: past about 4M points an iteration takes more node-range
+    // passes (join_passes) instead of more memory, so the buckets cost a
+    // fixed 2 KiB inline run per node plus the pool
+    constexpr int64_t kPoolMaxChunks = ((int64_t)16 << 30) / ((int64_t)kBucketRun * (int64_t)sizeof(uint64_t));
+    c->pool_chunks = (int)std::min<int64_t>(2 * n + 4096, kPoolMaxChunks);
     // test hook: a smaller pool drives proposals through the poisoned-run and
     // locked-insertion paths
     if (const char *e = std::getenv("KNNG_TEST_BUCKET_POOL_CHUNKS")) c->pool_chunks = std::max(1, std::atoi(e));
@@ -543,7 +547,7 @@ int join_passes(const knng_ctx *c, int it) {
     const double want = (double)c->n * m * (m - 1.0) * (it <= 1 ? 1.0 : 0.7);
     const double cap = 0.85 * ((double)c->n + (double)c->pool_chunks) * kBucketRun;
     const int p = (int)std::ceil(want / cap);
-    return std::max(1, std::min(p, 16));
+    return std::max(1, std::min(p, 64));
 }
 
 int enqueue_iteration(knng_ctx *c, bool gate) {
