@@ -247,6 +247,37 @@ typedef struct knng_desc {
 int knng_build_batched(const knng_desc *descs, int count, int K, float rho, float delta, int max_iters,
                        uint64_t seed, uint32_t flags, void *stream, knng_stats *stats);
 
+/* One data set of a batched build with its own parameters
+ * (knng_build_batched_ex); each field as the argument of knng_build_ex. */
+typedef struct knng_desc_ex {
+    const float *data;   /* n x d float32 points (host or device) */
+    int64_t n;
+    int32_t d;
+    int32_t K;           /* 1 <= K <= min(32, n - 1) */
+    float rho;           /* sample rate, (0, 1] */
+    float delta;         /* stopping threshold, >= 0 */
+    int32_t max_iters;   /* 0 .. 1000 */
+    uint64_t seed;
+    int32_t *ids;        /* n x K outputs (host or device), ids local to the data set */
+    float *dists;
+} knng_desc_ex;
+
+/*
+ * knng_build_batched with the parameters per data set (Section 2's method on
+ * many independent data sets; the batched call of the form descs, count,
+ * flags, stream).  Data sets with the same row-width class, K, sample size
+ * s = ceil(rho K), max_iters and seed share one batched run, in which each
+ * keeps its own delta (its own stopping count delta * n_b * K); the runs go
+ * one after the other on `stream`, ordered by width class.  Each result
+ * equals knng_build_ex of that data set with its own parameters and the
+ * shared flags.  Errors: KNNG_ERR_INVALID_ARG for a parameter out of range
+ * (checked for every descriptor before any work), KNNG_ERR_UNSUPPORTED for K >
+ * 32 or the relabelling flags; otherwise as knng_build_batched.  stats (may
+ * be NULL) sums the counters of all runs.  Returns when all outputs are
+ * written.
+ */
+int knng_build_batched_ex(const knng_desc_ex *descs, int count, uint32_t flags, void *stream, knng_stats *stats);
+
 /*
  * Exact K-NNG by brute force (Section 2: every distance, the K smallest per
  * point by (dist, id), float32 difference-form distances).  rows (host or

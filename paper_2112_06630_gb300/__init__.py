@@ -17,7 +17,8 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "KnngError", "Stats", "Context", "knng_build", "knng_build_batched", "knng_bruteforce", "lib_path", "Desc",
+    "KnngError", "Stats", "Context", "knng_build", "knng_build_batched", "knng_build_batched_ex", "knng_bruteforce",
+    "lib_path", "Desc", "DescEx",
     "bruteforce_last_fallbacks", "bruteforce_last_prefilter_ms", "measure_l2_read",
     "FLAG_REORDER", "FLAG_REORDER_B", "FLAG_TIMING", "FLAG_GRAPH", "FLAG_BF16", "FLAG_AUTOTUNE", "FLAG_HEAP_SAMPLING", "FLAG_REORDER_PARALLEL", "FLAG_FP8", "version", "strerror", "load",
 ]
@@ -64,6 +65,12 @@ class Desc(ctypes.Structure):
                 ("ids", ctypes.c_void_p), ("dists", ctypes.c_void_p)]
 
 
+class DescEx(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("rho", ctypes.c_float), ("delta", ctypes.c_float), ("max_iters", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("ids", ctypes.c_void_p), ("dists", ctypes.c_void_p)]
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -96,6 +103,7 @@ def _load():
         "knng_bruteforce_last_prefilter_ms": (f32, []),
         "knng_measure_l2_read": (i32, [i64, i32, P, ctypes.POINTER(ctypes.c_double)]),
         "knng_build_batched": (i32, [P, i32, i32, f32, f32, i32, u64, u32, P, P]),
+        "knng_build_batched_ex": (i32, [P, i32, u32, P, P]),
         "knng_strerror": (ctypes.c_char_p, [i32]),
         "knng_version": (ctypes.c_char_p, []),
     }
@@ -228,6 +236,32 @@ def knng_build_batched(datasets, K: int, rho: float = 1.0, delta: float = 0.001,
     rc = _lib.knng_build_batched(ctypes.addressof(descs), len(datasets), K, rho, delta, max_iters, seed, flags,
                                  _stream_ptr(stream, dev_any), ctypes.byref(st))
     _check(rc, "knng_build_batched")
+    info = st.as_dict()
+    info["overflow_warning"] = rc == WARN_OVERFLOW
+    return outs, info
+
+
+def knng_build_batched_ex(items, flags: int = 0, stream=None):
+    """knng_build_batched with parameters per data set.  `items`: sequence of
+    dicts with keys data (an (n_b, d_b) float32 array or CUDA tensor), K, rho,
+    delta, max_iters and seed.  Returns ([(ids, dists) per data set],
+    stats_dict)."""
+    keep, outs = [], []
+    descs = (DescEx * len(items))()
+    dev_any = False
+    for b, it in enumerate(items):
+        ptr, k, n, d, dev = _as_input(it["data"])
+        dev_any = dev_any or dev
+        K = int(it["K"])
+        ids, dists, ip, dp = _outputs(n, K, dev, k if dev else None)
+        keep.append(k)
+        outs.append((ids, dists))
+        descs[b] = DescEx(ptr, n, d, K, float(it["rho"]), float(it["delta"]), int(it["max_iters"]),
+                          int(it["seed"]), ip, dp)
+    st = Stats()
+    rc = _lib.knng_build_batched_ex(ctypes.addressof(descs), len(items), flags, _stream_ptr(stream, dev_any),
+                                    ctypes.byref(st))
+    _check(rc, "knng_build_batched_ex")
     info = st.as_dict()
     info["overflow_warning"] = rc == WARN_OVERFLOW
     return outs, info

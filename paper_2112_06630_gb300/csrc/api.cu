@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "../../include/knng.h"
@@ -955,9 +956,12 @@ int knng_build(const float *data, int64_t n, int d, int K, float rho, float delt
 
 namespace {
 
-// One batched build over data sets of one row-width class (below).
+// One batched build over data sets of one row-width class (below) that share
+// K, the sample size, max_iters and the seed; deltas (may be NULL: delta for
+// all) gives each data set its own stopping count.
 int build_batched_group(const knng_desc *descs, int count, int K, float rho, float delta, int max_iters,
-                        uint64_t seed, uint32_t flags, void *stream, knng_stats *stats) {
+                        uint64_t seed, uint32_t flags, void *stream, knng_stats *stats,
+                        const float *deltas = nullptr) {
     int64_t ntot = 0;
     int dmax = 0;
     std::vector<long long> off(count + 1);
@@ -968,7 +972,7 @@ int build_batched_group(const knng_desc *descs, int count, int K, float rho, flo
         if (!e.data || !e.ids || !e.dists || e.n < 2 || e.d < 1 || K > e.n - 1) return KNNG_ERR_INVALID_ARG;
         off[b] = ntot;
         nn[b] = (int)e.n;
-        thr[b] = (double)delta * (double)e.n * (double)K;
+        thr[b] = (double)(deltas ? deltas[b] : delta) * (double)e.n * (double)K;
         ntot += e.n;
         dmax = std::max(dmax, e.d);
     }
@@ -1119,6 +1123,48 @@ int knng_build_batched(const knng_desc *descs, int count, int K, float rho, floa
         knng_stats gs;
         const int r = build_batched_group(g.data(), (int)g.size(), K, rho, delta, max_iters, seed, flags, stream,
                                           stats ? &gs : nullptr);
+        if (r < 0) return r;
+        if (r > 0) rc = r;
+        if (stats) add_stats(total, gs);
+    }
+    if (stats) *stats = total;
+    return rc;
+}
+
+int knng_build_batched_ex(const knng_desc_ex *descs, int count, uint32_t flags, void *stream, knng_stats *stats) {
+    if (!descs || count < 1) return KNNG_ERR_INVALID_ARG;
+    if (flags & (KNNG_FLAG_REORDER | KNNG_FLAG_REORDER_B)) return KNNG_ERR_UNSUPPORTED;
+    for (int b = 0; b < count; ++b) {
+        const knng_desc_ex &e = descs[b];
+        if (!e.data || !e.ids || !e.dists || e.n < 2 || e.d < 1 || e.K < 1 || !(e.rho > 0.f && e.rho <= 1.f) ||
+            !(e.delta >= 0.f) || e.max_iters < 0 || e.max_iters > kMaxItersArg)
+            return KNNG_ERR_INVALID_ARG;
+        if (e.K > kMaxK) return KNNG_ERR_UNSUPPORTED;
+        if (e.K > e.n - 1) return KNNG_ERR_INVALID_ARG;
+    }
+    // one batched build per (row-width class, K, sample size, max_iters,
+    // seed), in that order; delta stays per data set
+    using GroupKey = std::tuple<int, int, int, int, uint64_t>;
+    std::map<GroupKey, std::vector<int>> groups;
+    for (int b = 0; b < count; ++b) {
+        const knng_desc_ex &e = descs[b];
+        groups[GroupKey(width_class(e.d), e.K, sample_size(e.rho, e.K), e.max_iters, e.seed)].push_back(b);
+    }
+    knng_stats total;
+    std::memset(&total, 0, sizeof(total));
+    int rc = KNNG_OK;
+    for (const auto &kv : groups) {
+        std::vector<knng_desc> g;
+        std::vector<float> deltas;
+        for (int b : kv.second) {
+            const knng_desc_ex &e = descs[b];
+            g.push_back(knng_desc{e.data, e.n, e.d, e.ids, e.dists});
+            deltas.push_back(e.delta);
+        }
+        const knng_desc_ex &f = descs[kv.second[0]];
+        knng_stats gs;
+        const int r = build_batched_group(g.data(), (int)g.size(), f.K, f.rho, f.delta, f.max_iters, f.seed, flags,
+                                          stream, stats ? &gs : nullptr, deltas.data());
         if (r < 0) return r;
         if (r > 0) rc = r;
         if (stats) add_stats(total, gs);

@@ -100,3 +100,53 @@ def test_header_compiles_as_c11(tmp_path):
                         str(tmp_path / "use_knng.o"), f"-I{os.path.join(ROOT, 'include')}", f"-I{cuda_inc}"],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_descriptor_layouts_match_the_binding(tmp_path):
+    """The ctypes descriptors of the binding have the C structs' size and
+    field offsets (a plain C program prints them)."""
+    import shutil
+    import subprocess
+    import paper_2112_06630_gb300 as knng
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not available")
+    structs = {"knng_desc": knng.Desc, "knng_desc_ex": knng.DescEx}
+    body = ""
+    for cname, py in structs.items():
+        body += f'    printf("{cname} size %zu\\n", sizeof({cname}));\n'
+        for f, _ in py._fields_:
+            body += f'    printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));\n'
+    src = tmp_path / "layout.c"
+    src.write_text('#include "knng.h"\n#include <stddef.h>\n#include <stdio.h>\nint main(void) {\n' + body
+                   + "    return 0;\n}\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", str(src), "-o", str(exe),
+                        f"-I{os.path.join(ROOT, 'include')}", "-I/usr/local/cuda/include"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    want = []
+    for cname, py in structs.items():
+        want.append(f"{cname} size {ctypes.sizeof(py)}")
+        want += [f"{cname} {f} {getattr(py, f).offset}" for f, _ in py._fields_]
+    assert [g for g in got if g] == want
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("rho", 0.0, -1), ("rho", 1.5, -1), ("delta", -1.0, -1), ("max_iters", -1, -1), ("K", 0, -1),
+    ("K", 10, -1),     # K > n - 1
+    ("d", 0, -1), ("K", 40, -5),
+])
+def test_batched_ex_rejects_any_bad_descriptor_before_device_work(lib, field, value, code):
+    """knng_build_batched_ex checks every descriptor before any work: one bad
+    descriptor after a good one fails the whole call."""
+    import paper_2112_06630_gb300 as knng
+    x = np.zeros((10, 4), np.float32)
+    ids = np.zeros((10, 40), np.int32)
+    dists = np.zeros((10, 40), np.float32)
+    good = dict(data=x.ctypes.data, n=10, d=4, K=3, rho=0.5, delta=0.001, max_iters=5, seed=0,
+                ids=ids.ctypes.data, dists=dists.ctypes.data)
+    bad = dict(good, **{field: value})
+    descs = (knng.DescEx * 2)(knng.DescEx(**good), knng.DescEx(**bad))
+    assert lib.knng_build_batched_ex(ctypes.addressof(descs), 2, 0, None, None) == code

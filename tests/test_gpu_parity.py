@@ -518,6 +518,26 @@ def test_batched_equals_single_builds_float_data():
 
 # -------------------------------------------------------------- autotuner ----
 
+def test_batched_ex_per_data_set_parameters_equal_single_builds():
+    """knng_build_batched_ex with K, rho, delta, max_iters and seed per data
+    set: data sets that share (width class, K, sample size, max_iters, seed)
+    run together with their own delta, the others in runs of their own; every
+    result equals that data set's own build bit for bit."""
+    params = [(3000, 24, 16, 0.5, 0.001, 8, 1), (2500, 24, 16, 0.5, 0.01, 8, 1), (2000, 24, 16, 0.52, 0.0, 8, 1),
+              (1800, 72, 20, 0.6, 0.001, 6, 7), (2200, 72, 12, 1.0, 0.002, 10, 3), (900, 150, 8, 0.3, 0.001, 5, 0),
+              (1200, 24, 32, 0.7, 0.001, 8, 1)]
+    items, sets = [], []
+    for b, (n, d, K, rho, delta, it, seed) in enumerate(params):
+        x = _cuda(workloads.gaussian_mixture(n, d, 8, seed=50 + b))
+        sets.append(x)
+        items.append(dict(data=x, K=K, rho=rho, delta=delta, max_iters=it, seed=seed))
+    outs, st = knng.knng_build_batched_ex(items)
+    assert st["lock_timeouts"] == 0
+    for it, (bi, bd) in zip(items, outs):
+        si, sd, _ = knng.knng_build(it["data"], it["K"], it["rho"], it["delta"], it["max_iters"], seed=it["seed"])
+        assert torch.equal(bi, si) and torch.equal(bd, sd), (it["K"], it["rho"], it["delta"])
+
+
 def test_autotuned_builds_equal_default_builds():
     """KNNG_FLAG_AUTOTUNE times every eligible join kernel on the first
     iteration, undoes each trial and keeps the fastest: the graph is the same
