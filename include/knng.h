@@ -30,8 +30,12 @@
  *     the positive warning KNNG_WARN_OVERFLOW (result valid, but some sampled
  *     candidates did not fit their fixed capacity and were skipped).  No C++
  *     exception crosses this boundary.  knng_strerror names a code.
- *   - Limits: 2 <= n < 2^30 - 1, 1 <= d, 1 <= K <= min(32, n - 1),
- *     0 < rho <= 1, delta >= 0, 0 <= max_iters <= 1000.
+ *   - Limits: 2 <= n < 2^30 - 1, 1 <= d, 1 <= K <= min(64, n - 1),
+ *     0 < rho <= 1, delta >= 0, 0 <= max_iters <= 1000.  K up to 32 holds a
+ *     list one key per lane of a warp, K of 33 to 64 two keys per lane; the
+ *     latter builds float32 keys with turbosampling only (KNNG_FLAG_BF16,
+ *     KNNG_FLAG_FP8 and KNNG_FLAG_HEAP_SAMPLING with K > 32 return
+ *     KNNG_ERR_UNSUPPORTED, as does K > 64).
  */
 #ifndef KNNG_H_
 #define KNNG_H_
@@ -253,7 +257,7 @@ typedef struct knng_desc_ex {
     const float *data;   /* n x d float32 points (host or device) */
     int64_t n;
     int32_t d;
-    int32_t K;           /* 1 <= K <= min(32, n - 1) */
+    int32_t K;           /* 1 <= K <= min(64, n - 1) */
     float rho;           /* sample rate, (0, 1] */
     float delta;         /* stopping threshold, >= 0 */
     int32_t max_iters;   /* 0 .. 1000 */
@@ -271,10 +275,10 @@ typedef struct knng_desc_ex {
  * one after the other on `stream`, ordered by width class.  Each result
  * equals knng_build_ex of that data set with its own parameters and the
  * shared flags.  Errors: KNNG_ERR_INVALID_ARG for a parameter out of range
- * (checked for every descriptor before any work), KNNG_ERR_UNSUPPORTED for K >
- * 32 or the relabelling flags; otherwise as knng_build_batched.  stats (may
- * be NULL) sums the counters of all runs.  Returns when all outputs are
- * written.
+ * (checked for every descriptor before any work), KNNG_ERR_UNSUPPORTED for
+ * K > 64 (or K > 32 with a low-precision or heap flag) or the relabelling
+ * flags; otherwise as knng_build_batched.  stats (may be NULL) sums the
+ * counters of all runs.  Returns when all outputs are written.
  */
 int knng_build_batched_ex(const knng_desc_ex *descs, int count, uint32_t flags, void *stream, knng_stats *stats);
 
@@ -282,10 +286,12 @@ int knng_build_batched_ex(const knng_desc_ex *descs, int count, uint32_t flags, 
  * Exact K-NNG by brute force (Section 2: every distance, the K smallest per
  * point by (dist, id), float32 difference-form distances).  rows (host or
  * device int64, may be NULL = all n rows) selects nq query points; outputs
- * are nq x K.  Ground truth for recall.  For rows of at most 128 floats and
- * n >= 4096 the call waits for the stream before it returns (it reads how many
- * queries the exact kernel must redo; see knng_bruteforce_last_fallbacks);
- * otherwise it only enqueues work when ids and dists are device pointers.
+ * are nq x K.  Ground truth for recall.  For rows of at most 128 floats,
+ * n >= 4096 and K <= 32 the call waits for the stream before it returns (the
+ * tensor-core prefilter: it reads how many queries the exact kernel must
+ * redo; see knng_bruteforce_last_fallbacks); otherwise (the exact kernel; for
+ * K > 32 one thread per query over all points) it only enqueues work when ids
+ * and dists are device pointers.
  */
 int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *rows,
                     int64_t nq, int32_t *ids, float *dists, void *stream);
@@ -336,7 +342,8 @@ int knng_measure_l2_read(int64_t bytes, int passes, void *stream, double *gbs);
  * The only scratch, the zero-padded copy of the points, is a static device
  * array of KNNG_NOALLOC_SCRATCH_BYTES that every GPU loading the library
  * holds until the process exits.  Returns KNNG_ERR_INVALID_ARG when
- * n * round_up(d, 4) * 4 exceeds KNNG_NOALLOC_SCRATCH_BYTES.
+ * n * round_up(d, 4) * 4 exceeds KNNG_NOALLOC_SCRATCH_BYTES, and
+ * KNNG_ERR_UNSUPPORTED for K > 32.
  *
  * The first call in a CUDA context (the first on a device, and the first
  * after a device reset, which makes a new context) does a set-up that
@@ -344,8 +351,8 @@ int knng_measure_l2_read(int64_t bytes, int passes, void *stream, double *gbs);
  * cudaGetSymbolAddress), loads every kernel the call can use and opts them in
  * to their shared memory.  Make that first call before any stream capture;
  * later calls only enqueue kernels (rows of more than 16,384 floats may still
- * set a kernel's shared-memory attribute on their first call).  All calls share the one array and it
- * keeps the last call's contents; each call overwrites the whole region it
+ * set a kernel's shared-memory attribute on their first call).  All calls
+ * share the one array and it keeps the last call's contents; each call overwrites the whole region it
  * reads before reading it.  Calls whose work overlaps on the GPU (other
  * streams, other threads) race on the array: serialise them.  Enqueues on
  * `stream`, does not synchronise.

@@ -355,6 +355,11 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
     *out = nullptr;
     int rc = check_args(n, d, K, rho, delta);
     if (rc) return rc;
+    // lists of more than 32 keys: float32 keys with turbosampling only (the
+    // low-precision forms resolve keys per id, and heap selection keeps its
+    // lists one per lane)
+    if (K > kLaneK && (flags & (KNNG_FLAG_BF16 | KNNG_FLAG_FP8 | KNNG_FLAG_HEAP_SAMPLING)))
+        return KNNG_ERR_UNSUPPORTED;
     knng_ctx *c = new (std::nothrow) knng_ctx();
     if (!c) return KNNG_ERR_OOM;
     c->n = n;
@@ -616,7 +621,7 @@ const char *knng_strerror(int code) {
         case KNNG_ERR_OOM: return "out of device memory";
         case KNNG_ERR_CUDA: return "CUDA error";
         case KNNG_ERR_TIMEOUT: return "a bounded device wait gave up";
-        case KNNG_ERR_UNSUPPORTED: return "unsupported parameters (K > 32)";
+        case KNNG_ERR_UNSUPPORTED: return "unsupported parameters (K > 64, or K > 32 with a low-precision or heap flag)";
         case KNNG_ERR_STATE: return "call not valid in the context's state";
         case KNNG_ERR_INTERNAL: return "internal error";
         default: return "unknown code";
@@ -1140,6 +1145,8 @@ int knng_build_batched_ex(const knng_desc_ex *descs, int count, uint32_t flags, 
             !(e.delta >= 0.f) || e.max_iters < 0 || e.max_iters > kMaxItersArg)
             return KNNG_ERR_INVALID_ARG;
         if (e.K > kMaxK) return KNNG_ERR_UNSUPPORTED;
+        if (e.K > kLaneK && (flags & (KNNG_FLAG_BF16 | KNNG_FLAG_FP8 | KNNG_FLAG_HEAP_SAMPLING)))
+            return KNNG_ERR_UNSUPPORTED;
         if (e.K > e.n - 1) return KNNG_ERR_INVALID_ARG;
     }
     // one batched build per (row-width class, K, sample size, max_iters,
@@ -1215,7 +1222,8 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
     const size_t ib = align256(sizeof(int32_t) * nq * K), db = align256(sizeof(float) * nq * K);
     const bool dev_out = is_device_ptr(ids) && is_device_ptr(dists);
     // slices of the point set when there are too few queries to fill the GPU
-    const int S = bruteforce_slices(n, nq);
+    // (their lists are merged one key per lane: K <= 32)
+    const int S = K > kLaneK ? 1 : bruteforce_slices(n, nq);
     const size_t pb = S > 1 ? sizeof(uint64_t) * (size_t)nq * S * K : 0;
     unsigned char *tmp = nullptr;
     KNNG_TRY(lib_malloc((void **)&tmp, xb + rb + (dev_out ? 0 : ib + db) + pb, s));
@@ -1248,9 +1256,9 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
     // tensor-core prefilter with exact re-rank where the rows allow it
     // (KNNG_TEST_BF_PATH=cuda|tensor forces a path in tests)
     const char *force = std::getenv("KNNG_TEST_BF_PATH");
-    bool tc = bruteforce_tc_supported(dp) && n >= 4096;
+    bool tc = bruteforce_tc_supported(dp) && n >= 4096 && K <= kLaneK;
     if (force && !std::strcmp(force, "cuda")) tc = false;
-    if (force && !std::strcmp(force, "tensor")) tc = bruteforce_tc_supported(dp);
+    if (force && !std::strcmp(force, "tensor")) tc = bruteforce_tc_supported(dp) && K <= kLaneK;
     g_bf_fallbacks = -1;
     g_bf_prefilter_ms = -1.f;
     if (e == cudaSuccess && tc) {

@@ -179,7 +179,8 @@ cudaError_t launch_bruteforce(const float *X, int64_t n, int dp, int K, const in
     if (K <= 8) return launch_bf_k<8>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
     if (K <= 16) return launch_bf_k<16>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
     if (K <= 24) return launch_bf_k<24>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
-    return launch_bf_k<32>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
+    if (K <= 32) return launch_bf_k<32>(X, n, nv, K, rows, nq, ids, dists, s, part, S);
+    return launch_bf_k<64>(X, n, nv, K, rows, nq, ids, dists, s, nullptr, 1);  // one slice: no list merge
 }
 
 namespace {
@@ -267,7 +268,7 @@ bool noalloc_pointer_ok(const void *p, int dev, int concurrent_managed) {
 extern "C" int knng_bruteforce_noalloc(const float *data, int64_t n, int d, int K, const int64_t *rows, int64_t nq,
                                        int32_t *ids, float *dists, void *stream) {
     if (!data || !ids || !dists || n < 2 || d < 1 || K < 1 || K > n - 1) return KNNG_ERR_INVALID_ARG;
-    if (K > knng::kMaxK) return KNNG_ERR_UNSUPPORTED;
+    if (K > knng::kLaneK) return KNNG_ERR_UNSUPPORTED;
     const int dp = (d + 3) & ~3;
     if ((uint64_t)n * (uint64_t)dp * sizeof(float) > (uint64_t)KNNG_NOALLOC_SCRATCH_BYTES)
         return KNNG_ERR_INVALID_ARG;

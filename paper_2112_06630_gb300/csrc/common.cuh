@@ -17,7 +17,8 @@ namespace knng {
 constexpr uint32_t kFlagNew = 1u;  // not yet sampled as a forward "new" candidate
 constexpr uint32_t kFlagIns = 2u;  // inserted during the current iteration
 constexpr uint64_t kKeyEmpty = ~0ull;
-constexpr int kMaxK = 32;
+constexpr int kMaxK = 64;        // lists of up to 64 keys: one key per lane up to 32, two above
+constexpr int kLaneK = 32;       // the largest K held one key per lane
 
 __host__ __device__ __forceinline__ uint64_t make_key(float dist, uint32_t id, uint32_t flags) {
 #ifdef __CUDA_ARCH__
@@ -124,6 +125,80 @@ __device__ __forceinline__ uint64_t warp_sort_u64(uint64_t v) {
         }
     }
     return v;
+}
+
+// Ascending bitonic sort of 64 keys held two per lane across the full warp:
+// a is element lane, b element lane + 32.
+__device__ __forceinline__ void warp_sort_u64x2(uint64_t &a, uint64_t &b) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 32) {
+                // k == 64: element lane against element lane + 32, ascending
+                const uint64_t mn = a < b ? a : b, mx = a < b ? b : a;
+                a = mn;
+                b = mx;
+                continue;
+            }
+            const bool low = (lane & j) == 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint64_t &v = h ? b : a;
+                const uint64_t o = shfl_xor_u64(v, j);
+                const bool up = (((int)lane + 32 * h) & k) == 0;
+                const uint64_t mn = v < o ? v : o, mx = v < o ? o : v;
+                v = (low == up) ? mn : mx;
+            }
+        }
+    }
+}
+
+// A list of K <= 64 ascending keys held by one warp: entry lane in lo, entry
+// lane + 32 in hi (kKeyEmpty at and past K).  For K <= 32 hi stays empty and
+// every operation is the one-key-per-lane form.
+struct WList {
+    uint64_t lo, hi;
+};
+__device__ __forceinline__ WList wlist_load(const uint64_t *row, int K) {
+    const int lane = (int)lane_id();
+    WList L;
+    L.lo = lane < K ? __ldcg(row + lane) : kKeyEmpty;
+    L.hi = lane + 32 < K ? __ldcg(row + 32 + lane) : kKeyEmpty;
+    return L;
+}
+__device__ __forceinline__ void wlist_store(const WList &L, uint64_t *row, int K) {
+    const int lane = (int)lane_id();
+    if (lane < K) __stcg(row + lane, L.lo);
+    if (lane + 32 < K) __stcg(row + 32 + lane, L.hi);
+}
+// entry idx (the same on every lane)
+__device__ __forceinline__ uint64_t wlist_at(const WList &L, int idx) {
+    const uint64_t a = __shfl_sync(0xFFFFFFFFu, L.lo, idx & 31), b = __shfl_sync(0xFFFFFFFFu, L.hi, idx & 31);
+    return idx < 32 ? a : b;
+}
+// entries carrying all bits of `flag`
+__device__ __forceinline__ int wlist_count(const WList &L, int K, uint64_t flag) {
+    const int lane = (int)lane_id();
+    return __popc(__ballot_sync(0xFFFFFFFFu, lane < K && (L.lo & flag) == flag)) +
+           __popc(__ballot_sync(0xFFFFFFFFu, lane + 32 < K && (L.hi & flag) == flag));
+}
+// Insert x if it orders before the worst entry and its id is not listed; the
+// worst entry leaves.  Warp-uniform result: true if inserted.
+__device__ __forceinline__ bool wlist_insert(WList &L, uint64_t x, int K) {
+    const int lane = (int)lane_id();
+    const bool vl = lane < K, vh = lane + 32 < K;
+    if (x >= wlist_at(L, K - 1)) return false;
+    const uint32_t id = key_id(x);
+    if (__any_sync(0xFFFFFFFFu, (vl && key_id(L.lo) == id) || (vh && key_id(L.hi) == id))) return false;
+    const unsigned gl = __ballot_sync(0xFFFFFFFFu, vl && L.lo > x), gh = __ballot_sync(0xFFFFFFFFu, vh && L.hi > x);
+    const int pos = gl ? __ffs(gl) - 1 : 32 + __ffs(gh) - 1;  // first entry ordered after x
+    const uint64_t lo_up = __shfl_up_sync(0xFFFFFFFFu, L.lo, 1), hi_up = __shfl_up_sync(0xFFFFFFFFu, L.hi, 1);
+    const uint64_t lo_last = __shfl_sync(0xFFFFFFFFu, L.lo, 31);
+    if (vl && lane >= pos) L.lo = lane == pos ? x : lo_up;
+    if (vh && lane + 32 >= pos) L.hi = lane + 32 == pos ? x : (lane == 0 ? lo_last : hi_up);
+    return true;
 }
 
 template <typename T>

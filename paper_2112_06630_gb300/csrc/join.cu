@@ -67,7 +67,7 @@ __host__ __device__ inline JoinLayout join_layout(int cap, int nv, bool rows_sme
     L.row_stride = (nv % 2 == 0) ? nv + 1 : nv;
     L.off_swk = kSetMax * 4 * 2;
     L.off_rows = L.off_swk + kSetMax * 8 * 2;
-    const size_t dedup = (size_t)L.raw_max * 4 + (4u << kHashBits);
+    const size_t dedup = (size_t)L.raw_max * 4 + (4u << hash_bits(cap));
     const size_t rows = rows_smem ? (size_t)kSetMax * L.row_stride * 16 : 0;
     L.per_warp = L.off_rows + (dedup > rows ? dedup : rows);
     L.per_warp = (L.per_warp + 15) & ~(size_t)15;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kJoinWarps * 32, 8) join_kernel(DevState st, i
     unsigned *mw = reinterpret_cast<unsigned *>(mask);  // the masks as 32-bit words (native shared atomics)
     float4 *rows = reinterpret_cast<float4 *>(wbase + lay.off_rows);
     int *hset = reinterpret_cast<int *>(wbase + lay.off_rows);  // aliases rows until they are staged
-    int *raw = hset + (1 << kHashBits);
+    int *raw = hset + (1 << hash_bits(st.cap));
     const int rs = lay.row_stride;
     const float4 *X4 = reinterpret_cast<const float4 *>(st.X);
 
@@ -424,12 +424,37 @@ __device__ __forceinline__ int merge_batch(uint64_t &Lk, uint64_t x, int K, bool
     return ins;
 }
 
-// One warp per node with proposals: merge its bucket into its list.  The
-// bucket's inline run (up to 256 keys) is loaded two batches ahead of the
-// merges; pool runs (hub nodes) stream batch by batch.
+// Merge of up to 32 candidate keys (one per lane, kKeyEmpty = none) into a
+// list of K > 32 float32 keys held two per lane (WList): a key search over
+// the K entries drops the listed ones (a pair has one key), then the others
+// that order before the worst entry go in one at a time.
+__device__ __forceinline__ int merge_batch_wide(WList &L, uint64_t x, int K) {
+    const uint64_t xo = key_order(x);
+    int lo = 0, hi = K - 1;
+#pragma unroll
+    for (int step = 0; step < 6; ++step) {
+        const int mid = (lo + hi) >> 1;
+        const uint64_t a = __shfl_sync(kFull, L.lo, mid & 31), b = __shfl_sync(kFull, L.hi, mid & 31);
+        if (lo < hi) {
+            if (key_order(mid < 32 ? a : b) < xo) lo = mid + 1;
+            else hi = mid;
+        }
+    }
+    const uint64_t a = __shfl_sync(kFull, L.lo, lo & 31), b = __shfl_sync(kFull, L.hi, lo & 31);
+    const bool listed = key_order(lo < 32 ? a : b) == xo;
+    unsigned cand = __ballot_sync(kFull, x < wlist_at(L, K - 1) && !listed);
+    int ins = 0;
+    for (; cand; cand &= cand - 1) ins += wlist_insert(L, __shfl_sync(kFull, x, __ffs(cand) - 1), K);
+    return ins;
+}
+
+// One warp per node with proposals: merge its bucket into its list (KW keys
+// per lane).  The bucket's inline run (up to 256 keys) is loaded two batches
+// ahead of the merges; pool runs (hub nodes) stream batch by batch.
+template <int KW>
 __global__ void __launch_bounds__(kMergeWarps * 32, 4) merge_kernel(DevState st, int li) {
     if (iteration_skipped(st, li)) return;
-    __shared__ uint64_t scratch_all[kMergeWarps][kMaxK];
+    __shared__ uint64_t scratch_all[kMergeWarps][KW == 1 ? kLaneK : 1];  // the sort-merge of one-key-per-lane lists
     uint64_t *scratch = scratch_all[threadIdx.x >> 5];
     __shared__ long long bstat[3];
     if (threadIdx.x < 3) bstat[threadIdx.x] = 0;
@@ -450,12 +475,19 @@ __global__ void __launch_bounds__(kMergeWarps * 32, 4) merge_kernel(DevState st,
         const int cnt = min(cnt_all, kBucketMax);
         uint64_t *row = st.keys + (size_t)p * K;
         int *chunks = st.pchunk + (size_t)p * kBucketChunks;
-        uint64_t Lk = valid ? row[lane] : kKeyEmpty;
+        uint64_t Lk = kKeyEmpty;
+        WList L{kKeyEmpty, kKeyEmpty};
+        if constexpr (KW == 1) Lk = valid ? row[lane] : kKeyEmpty;
+        else L = wlist_load(row, K);
         // entries already inserted in this iteration (an earlier pass's merge
         // or a locked insertion, which counted them)
-        const int ch0 = __popc(__ballot_sync(kFull, valid && (Lk & kFlagIns)));
+        const int ch0 = KW == 1 ? __popc(__ballot_sync(kFull, valid && (Lk & kFlagIns))) : wlist_count(L, K, kFlagIns);
         int ins = 0;
         const bool bf16 = st.bf16 != 0;
+        auto merge = [&](uint64_t x) {
+            if constexpr (KW == 1) return merge_batch(Lk, x, K, bf16, scratch);
+            else return merge_batch_wide(L, x, K);
+        };
         // the inline run, its loads two batches ahead of the merges
         const uint64_t *run = st.pbucket + ((size_t)p << kBucketRunBits);
         const int c_in = min(cnt, kBucketRun);
@@ -465,7 +497,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32, 4) merge_kernel(DevState st,
             const uint64_t x = x0;
             x0 = x1;
             x1 = c0 + 64 + (int)lane < c_in ? __ldcs(run + c0 + 64 + lane) : kKeyEmpty;
-            ins += merge_batch(Lk, x, K, bf16, scratch);
+            ins += merge(x);
         }
         // pool runs (runs are multiples of 32 keys: a batch never straddles two)
         for (int c0 = kBucketRun; c0 < cnt; c0 += 32) {
@@ -480,12 +512,13 @@ __global__ void __launch_bounds__(kMergeWarps * 32, 4) merge_kernel(DevState st,
             if (!run) continue;
             const int off = c0 & (kBucketRun - 1);
             const uint64_t x = c0 + (int)lane < cnt ? __ldcs(run + off + lane) : kKeyEmpty;
-            ins += merge_batch(Lk, x, K, bf16, scratch);
+            ins += merge(x);
         }
         // entries flagged "inserted in this iteration" that are still listed
         // (the sampling pass cleared that flag everywhere before the join),
         // less those already counted
-        const int ch = __popc(__ballot_sync(kFull, valid && (Lk & kFlagIns))) - ch0;
+        const int ch =
+            (KW == 1 ? __popc(__ballot_sync(kFull, valid && (Lk & kFlagIns))) : wlist_count(L, K, kFlagIns)) - ch0;
         w_changes += ch;
         if (st.ds) {
             const int b = st.ds[p];
@@ -497,7 +530,11 @@ __global__ void __launch_bounds__(kMergeWarps * 32, 4) merge_kernel(DevState st,
             }
             cur_changes += ch;
         }
-        if (ins && valid) row[lane] = Lk;
+        if constexpr (KW == 1) {
+            if (ins && valid) row[lane] = Lk;
+        } else {
+            if (ins) wlist_store(L, row, K);
+        }
         w_ins += ins;
         ++w_merges;
     }
@@ -560,8 +597,13 @@ cudaError_t launch_join(const DevState &st, int li, cudaStream_t s) {
 }
 
 cudaError_t launch_merge(const DevState &st, int li, cudaStream_t s) {
-    const int grid = grid_for((const void *)merge_kernel, kMergeWarps * 32, 0);
-    merge_kernel<<<grid, kMergeWarps * 32, 0, s>>>(st, li);
+    if (st.K > kLaneK) {
+        const int grid = grid_for((const void *)merge_kernel<2>, kMergeWarps * 32, 0);
+        merge_kernel<2><<<grid, kMergeWarps * 32, 0, s>>>(st, li);
+        return cudaGetLastError();
+    }
+    const int grid = grid_for((const void *)merge_kernel<1>, kMergeWarps * 32, 0);
+    merge_kernel<1><<<grid, kMergeWarps * 32, 0, s>>>(st, li);
     return cudaGetLastError();
 }
 

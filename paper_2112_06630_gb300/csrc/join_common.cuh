@@ -26,7 +26,12 @@ __device__ __forceinline__ int nth_set_bit64(unsigned long long x, int r) {
     }
     return pos;
 }
-constexpr int kHashBits = 8;     // 256-slot hash set for repeat removal (at most 2 * (32 + 72) ids)
+// Hash set for repeat removal: 256 slots while a node's raw ids (at most
+// 2 cap, cap = K + 2s + 8) fit it, 512 for the larger capacities of K > 32
+// (at most 2 (64 + 136) = 400 ids).
+constexpr int kHashBits = 8;
+constexpr int kHashBitsMax = 9;
+__host__ __device__ __forceinline__ int hash_bits(int cap) { return 2 * cap <= (1 << kHashBits) ? kHashBits : kHashBitsMax; }
 constexpr int kLockSpins = 1 << 20;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
@@ -56,17 +61,18 @@ __device__ __forceinline__ bool warp_insert(uint64_t &Lk, uint64_t x, int K) {
     return true;
 }
 
-// Reverse part raw[b, b + cnt) (cnt <= 96; reverse capacities are at most
-// 2 * 32 + 8) put in a fixed order: ascending by (id - base) * 0x9E3779B1 mod
+// Reverse part raw[b, b + cnt) (cnt <= 32 H; reverse capacities are at most
+// 2 * 32 + 8 = 72 for K <= 32 and 2 * 64 + 8 = 136 above) put in a fixed order: ascending by (id - base) * 0x9E3779B1 mod
 // 2^32, a bijection of the ids local to the data set (base: its first node),
 // so the order is canonical, the same in a batched build, and not tied to id
 // size.  The ids of one reverse part are distinct (a node lists an id once).
+template <int H>
 __device__ __forceinline__ void warp_order_part(int *raw, int b, int cnt, uint32_t base) {
     const unsigned lane = lane_id();
-    int v[3], r[3];
-    uint32_t k[3];
+    int v[H], r[H];
+    uint32_t k[H];
 #pragma unroll
-    for (int h = 0; h < 3; ++h) {
+    for (int h = 0; h < H; ++h) {
         const int i = (int)lane + 32 * h;
         v[h] = i < cnt ? raw[b + i] : 0;
         k[h] = ((uint32_t)v[h] - base) * 0x9E3779B1u;
@@ -75,11 +81,11 @@ __device__ __forceinline__ void warp_order_part(int *raw, int b, int cnt, uint32
     for (int j = 0; j < cnt; ++j) {
         const uint32_t kj = ((uint32_t)raw[b + j] - base) * 0x9E3779B1u;
 #pragma unroll
-        for (int h = 0; h < 3; ++h) r[h] += kj < k[h];
+        for (int h = 0; h < H; ++h) r[h] += kj < k[h];
     }
     __syncwarp();
 #pragma unroll
-    for (int h = 0; h < 3; ++h)
+    for (int h = 0; h < H; ++h)
         if ((int)lane + 32 * h < cnt) raw[b + r[h]] = v[h];
     __syncwarp();
 }
@@ -93,9 +99,13 @@ __device__ __forceinline__ void warp_order_part(int *raw, int b, int cnt, uint32
 // warp_order_part: the forward parts are in list order already, so which ids
 // the cap drops does not depend on the order in which other warps took the
 // reverse slots, and the build stays deterministic.  raw must hold 2 * cap
-// ints and hset 2^kHashBits ints.  Lane 0 also restarts u's reverse degrees
+// ints and hset 2^hash_bits(cap) ints.  Lane 0 also restarts u's reverse degrees
 // for the next iteration.  Returns total raw ids read; ns = 0 when u has no
 // new candidate (no join pair).  Results are warp-uniform.
+// kWide: 0 = the form for reverse capacities up to 96 with a 256-slot hash
+// set, 1 = the form for the larger ones of K > 32, -1 = either, chosen at run
+// time (kernels that keep one instance for both).
+template <int kWide = -1>
 __device__ __forceinline__ int warp_gather_candidates(const DevState &st, long long u, int *raw, int *hset, int *sid,
                                                       int &ns_out, int &m_out, long long &setovf) {
     const unsigned lane = lane_id();
@@ -121,12 +131,19 @@ __device__ __forceinline__ int warp_gather_candidates(const DevState &st, long l
         else v = st.cand_old[cb + K + (idx - nnew_raw - fo)];
         raw[idx] = v;
     }
-    for (int i = lane; i < (1 << kHashBits); i += 32) hset[i] = -1;
+    const bool wide = kWide < 0 ? (R > 96 || hash_bits(st.cap) > kHashBits) : kWide == 1;
+    const int hb = wide ? hash_bits(st.cap) : kHashBits;
+    for (int i = lane; i < (1 << hb); i += 32) hset[i] = -1;
     __syncwarp();
     if (total > kSetMax) {
         const uint32_t base = (uint32_t)(u - node_local(st, u));
-        warp_order_part(raw, fn, rn, base);
-        warp_order_part(raw, nnew_raw + fo, ro, base);
+        if (!wide) {
+            warp_order_part<3>(raw, fn, rn, base);
+            warp_order_part<3>(raw, nnew_raw + fo, ro, base);
+        } else {
+            warp_order_part<5>(raw, fn, rn, base);
+            warp_order_part<5>(raw, nnew_raw + fo, ro, base);
+        }
     }
     int ns = 0, m = 0;
     for (int pass = 0; pass < 2; ++pass) {
@@ -138,15 +155,15 @@ __device__ __forceinline__ int warp_gather_candidates(const DevState &st, long l
             // of repeats within the batch only the lowest lane competes
             const unsigned grp = __match_any_sync(kFull, v);
             if (idx < hi_i && (grp & lanemask_lt()) == 0) {
-                unsigned h = ((unsigned)v * 0x9E3779B1u) >> (32 - kHashBits);
-                for (int probe = 0; probe < (1 << kHashBits); ++probe) {
+                unsigned h = ((unsigned)v * 0x9E3779B1u) >> (32 - hb);
+                for (int probe = 0; probe < (1 << hb); ++probe) {
                     const int prev = atomicCAS(hset + h, -1, v);
                     if (prev == -1) {
                         keep = true;
                         break;
                     }
                     if (prev == v) break;
-                    h = (h + 1) & ((1u << kHashBits) - 1);
+                    h = (h + 1) & ((1u << hb) - 1);
                 }
             }
             const unsigned km = __ballot_sync(kFull, keep);
@@ -192,20 +209,20 @@ __device__ __forceinline__ int warp_locked_insert(const DevState &st, uint32_t p
     got = __shfl_sync(kFull, got, 0);
     if (!got) return -1;
     uint64_t *row = st.keys + (size_t)p * K;
-    uint64_t Lk = (int)lane < K ? __ldcg(row + lane) : kKeyEmpty;
-    const int before = __popc(__ballot_sync(kFull, (int)lane < K && (Lk & kFlagIns)));
+    WList L = wlist_load(row, K);
+    const int before = wlist_count(L, K, kFlagIns);
     int ins = 0;
     for (unsigned long long mm = rest; mm; mm &= mm - 1) {
         const int j = __ffsll((long long)mm) - 1;
         const uint64_t xa = __shfl_sync(kFull, x0, j & 31), xb = __shfl_sync(kFull, x1, j & 31);
-        ins += warp_insert(Lk, j < 32 ? xa : xb, K);
+        ins += wlist_insert(L, j < 32 ? xa : xb, K);
     }
-    const int after = __popc(__ballot_sync(kFull, (int)lane < K && (Lk & kFlagIns)));
+    const int after = wlist_count(L, K, kFlagIns);
     if (lane == 0 && after != before) {
         atomic_add_ll(st.it_stats + (size_t)li * kItCount + kItChanges, after - before);
         if (st.ds) atomic_add_ll(st.ds_changes + (size_t)st.ds[p] * kMaxLocalIters + li, after - before);
     }
-    if ((int)lane < K) __stcg(row + lane, Lk);
+    wlist_store(L, row, K);
     __threadfence();
     __syncwarp();
     if (lane == 0) atomicExch(st.locks + p, 0);

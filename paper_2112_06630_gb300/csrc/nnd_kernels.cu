@@ -1,8 +1,9 @@
 // nnd_kernels.cu -- the NN-Descent steps around the local join: staging of
 // the points, random initialisation, degree counting, one-pass sampling, the
 // greedy relabelling (Algorithm 1) with its permutation, and the re-ranked
-// output.  One warp owns one node's list wherever a list is touched, so list
-// rows (K <= 32 keys) map onto lanes.
+// output.  One warp owns one node's list wherever a list is touched: list
+// entry k sits on lane k, and for K > 32 entry k + 32 on lane k too (the list
+// kernels take KW = 1 or 2 keys per lane).
 #include <map>
 #include <mutex>
 #include <utility>
@@ -109,7 +110,7 @@ cudaError_t current_context_id(unsigned long long *id) {
 // granted per (kernel, context) under a lock (a context made after a device
 // reset starts without any grant).
 cudaError_t smem_opt_in(const void *kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    if (bytes == 0) return cudaSuccess;
     unsigned long long ctx = 0;
     cudaError_t e = current_context_id(&ctx);
     if (e != cudaSuccess) {
@@ -117,13 +118,29 @@ cudaError_t smem_opt_in(const void *kernel, size_t bytes) {
         cudaGetLastError();
         return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     }
+    // without the attribute a launch may use 48 KB of shared memory, static
+    // and dynamic together: the kernel's static size is read once per context
+    struct Grant {
+        long long stat = -1;  // static shared memory of the kernel
+        size_t have = 0;      // dynamic bytes the kernel may use
+    };
     static std::mutex mu;
-    static std::map<std::pair<const void *, unsigned long long>, size_t> granted;
+    static std::map<std::pair<const void *, unsigned long long>, Grant> granted;
     std::lock_guard<std::mutex> g(mu);
-    size_t &have = granted[{kernel, ctx}];
-    if (have >= bytes) return cudaSuccess;
+    Grant &gr = granted[{kernel, ctx}];
+    if (gr.have >= bytes) return cudaSuccess;
+    if (gr.stat < 0) {
+        cudaFuncAttributes a;
+        e = cudaFuncGetAttributes(&a, kernel);
+        if (e != cudaSuccess) return e;
+        gr.stat = (long long)a.sharedSizeBytes;
+    }
+    if (bytes + (size_t)gr.stat <= 48 * 1024) {
+        gr.have = bytes;
+        return cudaSuccess;
+    }
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) have = bytes;
+    if (e == cudaSuccess) gr.have = bytes;
     return e;
 }
 
@@ -158,7 +175,7 @@ cudaError_t prepare_stage() {
 // taken in order and a proposal is accepted unless it is u or already chosen.
 // A warp evaluates 32 consecutive attempts at once and accepts, in lane order,
 // exactly the proposals the sequential rule would accept.
-template <bool kStaged>
+template <bool kStaged, int KW>
 __global__ void __launch_bounds__(kBlock) init_random_kernel(DevState st, uint64_t base, int *err) {
     __shared__ uint32_t chosen_s[kWarpsPerBlock][kMaxK];
     extern __shared__ __align__(16) float4 stage_sm[];
@@ -198,64 +215,107 @@ __global__ void __launch_bounds__(kBlock) init_random_kernel(DevState st, uint64
                 __syncwarp();
             }
         }
-        uint64_t key = kKeyEmpty;
-        const uint32_t v = (int)lane < K ? chosen[lane] : (uint32_t)u;
-        float dd;
-        if (kStaged) dd = warp_staged_dist(X4, st.nv, u, v, K, stage_sm + (threadIdx.x >> 5) * 33 * (st.nv | 1));
-        else dd = (int)lane < K ? l2sq_rows(X4 + (size_t)u * st.nv, X4 + (size_t)v * st.nv, st.nv) : 0.f;
-        if ((int)lane < K) key = make_key(dd, v, kFlagNew);
-        key = warp_sort_u64(key);
-        if ((int)lane < K) st.keys[(size_t)u * K + lane] = key;
+        // entries lane (and lane + 32): distances, keys, one sorted list
+        uint64_t key[KW];
+#pragma unroll
+        for (int h = 0; h < KW; ++h) {
+            const int k = (int)lane + 32 * h;
+            const int cnt = K - 32 * h < 32 ? K - 32 * h : 32;
+            const uint32_t v = k < K ? chosen[k] : (uint32_t)u;
+            float dd;
+            if (kStaged) dd = warp_staged_dist(X4, st.nv, u, v, cnt, stage_sm + (threadIdx.x >> 5) * 33 * (st.nv | 1));
+            else dd = k < K ? l2sq_rows(X4 + (size_t)u * st.nv, X4 + (size_t)v * st.nv, st.nv) : 0.f;
+            key[h] = k < K ? make_key(dd, v, kFlagNew) : kKeyEmpty;
+        }
+        if constexpr (KW == 2) warp_sort_u64x2(key[0], key[KW - 1]);
+        else key[0] = warp_sort_u64(key[0]);
+#pragma unroll
+        for (int h = 0; h < KW; ++h)
+            if ((int)lane + 32 * h < K) st.keys[(size_t)u * K + lane + 32 * h] = key[h];
         __syncwarp();
     }
 }
 
-cudaError_t launch_init_random(const DevState &st, uint64_t seed, int *err, cudaStream_t s) {
-    const uint64_t base = hash_base(seed, kStreamInit, 0);
+template <int KW>
+cudaError_t launch_init_random_t(const DevState &st, uint64_t base, int *err, cudaStream_t s) {
     if (st.nv >= kStageMinNv && st.nv <= kStageMaxNv) {
         const size_t dyn = stage_smem_bytes(st.nv);
-        cudaError_t e = smem_opt_in((const void *)init_random_kernel<true>, dyn);
+        cudaError_t e = smem_opt_in((const void *)init_random_kernel<true, KW>, dyn);
         if (e != cudaSuccess) return e;
-        const int grid = grid_for((const void *)init_random_kernel<true>, kStageWarps * 32, dyn);
-        init_random_kernel<true><<<grid, kStageWarps * 32, dyn, s>>>(st, base, err);
+        const int grid = grid_for((const void *)init_random_kernel<true, KW>, kStageWarps * 32, dyn);
+        init_random_kernel<true, KW><<<grid, kStageWarps * 32, dyn, s>>>(st, base, err);
         return cudaGetLastError();
     }
-    int grid = grid_for((const void *)init_random_kernel<false>, kBlock, 0);
-    init_random_kernel<false><<<grid, kBlock, 0, s>>>(st, base, err);
+    int grid = grid_for((const void *)init_random_kernel<false, KW>, kBlock, 0);
+    init_random_kernel<false, KW><<<grid, kBlock, 0, s>>>(st, base, err);
     return cudaGetLastError();
+}
+
+cudaError_t launch_init_random(const DevState &st, uint64_t seed, int *err, cudaStream_t s) {
+    const uint64_t base = hash_base(seed, kStreamInit, 0);
+    return st.K > kLaneK ? launch_init_random_t<2>(st, base, err, s) : launch_init_random_t<1>(st, base, err, s);
 }
 
 // Lists from a given graph: validate (in range, != u, distinct), compute
 // distances, sort.  err |= 2 on an invalid row.
+template <int KW>
 __global__ void __launch_bounds__(kBlock) init_graph_kernel(DevState st, const int32_t *__restrict__ ids,
                                                             const uint8_t *__restrict__ is_new, int *err) {
     const unsigned lane = lane_id();
     const int K = st.K;
     const float4 *X4 = reinterpret_cast<const float4 *>(st.X);
     for (long long u = gwarp(); u < st.n; u += nwarps()) {
-        bool valid = (int)lane < K;
-        int32_t v = valid ? ids[(size_t)u * K + lane] : -1 - (int)lane;
-        bool bad = valid && (v < 0 || v >= st.n || v == u);
-        unsigned same = __match_any_sync(kFull, v);
-        bad = bad || (valid && __popc(same) > 1);
+        int32_t v[KW];
+        bool bad = false;
+#pragma unroll
+        for (int h = 0; h < KW; ++h) {
+            const int k = (int)lane + 32 * h;
+            const bool valid = k < K;
+            v[h] = valid ? ids[(size_t)u * K + k] : -1 - k;  // distinct negatives off the list
+            // every lane takes part in the warp-wide match (never under a
+            // short-circuit: the collective needs the whole warp)
+            const unsigned same = __match_any_sync(kFull, v[h]);
+            bad = bad || (valid && (v[h] < 0 || v[h] >= st.n || v[h] == u || __popc(same) > 1));
+        }
+        if constexpr (KW == 2) {
+            // repeats between the two halves
+            for (int j = 0; j < 32; ++j) {
+                const int32_t vj = __shfl_sync(kFull, v[0], j);
+                bad = bad || ((int)lane + 32 < K && v[1] == vj);
+            }
+        }
         if (__any_sync(kFull, bad)) {
             if (lane == 0) atomicOr(err, 2);
-            v = valid ? (int32_t)((u + 1 + lane) % st.n) : 0;
+#pragma unroll
+            for (int h = 0; h < KW; ++h) v[h] = (int)lane + 32 * h < K ? (int32_t)((u + 1 + lane + 32 * h) % st.n) : 0;
         }
-        uint64_t key = kKeyEmpty;
-        if (valid) {
-            float dd = l2sq_rows(X4 + (size_t)u * st.nv, X4 + (size_t)v * st.nv, st.nv);
-            key = make_key(dd, (uint32_t)v, is_new[(size_t)u * K + lane] ? kFlagNew : 0u);
+        uint64_t key[KW];
+#pragma unroll
+        for (int h = 0; h < KW; ++h) {
+            const int k = (int)lane + 32 * h;
+            key[h] = kKeyEmpty;
+            if (k < K) {
+                const float dd = l2sq_rows(X4 + (size_t)u * st.nv, X4 + (size_t)v[h] * st.nv, st.nv);
+                key[h] = make_key(dd, (uint32_t)v[h], is_new[(size_t)u * K + k] ? kFlagNew : 0u);
+            }
         }
-        key = warp_sort_u64(key);
-        if (valid) st.keys[(size_t)u * K + lane] = key;
+        if constexpr (KW == 2) warp_sort_u64x2(key[0], key[KW - 1]);
+        else key[0] = warp_sort_u64(key[0]);
+#pragma unroll
+        for (int h = 0; h < KW; ++h)
+            if ((int)lane + 32 * h < K) st.keys[(size_t)u * K + lane + 32 * h] = key[h];
     }
 }
 
 cudaError_t launch_init_graph(const DevState &st, const int32_t *ids, const uint8_t *is_new, int *err,
                               cudaStream_t s) {
-    int grid = grid_for((const void *)init_graph_kernel, kBlock, 0);
-    init_graph_kernel<<<grid, kBlock, 0, s>>>(st, ids, is_new, err);
+    if (st.K > kLaneK) {
+        int grid = grid_for((const void *)init_graph_kernel<2>, kBlock, 0);
+        init_graph_kernel<2><<<grid, kBlock, 0, s>>>(st, ids, is_new, err);
+        return cudaGetLastError();
+    }
+    int grid = grid_for((const void *)init_graph_kernel<1>, kBlock, 0);
+    init_graph_kernel<1><<<grid, kBlock, 0, s>>>(st, ids, is_new, err);
     return cudaGetLastError();
 }
 
@@ -299,6 +359,7 @@ cudaError_t launch_count(const DevState &st, int li, cudaStream_t s) {
 // "inserted this iteration" flag.  Forward candidates are written compacted
 // by u's warp; reverse ones take an atomic slot in v's reverse part (capacity
 // R, overflow counted).
+template <int KW>
 __global__ void __launch_bounds__(kBlock) sample_kernel(DevState st, int li, uint64_t fbase, uint64_t rbase) {
     if (iteration_skipped(st, li)) return;
     const unsigned lane = lane_id();
@@ -308,34 +369,49 @@ __global__ void __launch_bounds__(kBlock) sample_kernel(DevState st, int li, uin
     for (long long u = gwarp(); u < st.n; u += nwarps()) {
         if (node_skipped(st, u, li)) continue;
         const uint64_t ul = (uint64_t)node_local(st, u);
-        const bool valid = (int)lane < K;
-        uint64_t key = valid ? st.keys[(size_t)u * K + lane] : kKeyEmpty;
-        const bool isnew = valid && (key & kFlagNew);
-        const unsigned nm = __ballot_sync(kFull, isnew);
-        const uint32_t cnew = __popc(nm), cold = (uint32_t)K - cnew;
-        const uint32_t v = key_id(key);
-        bool accf = false;
-        if (valid) accf = accept(hash_uj(fbase, ul, lane), isnew ? cnew : cold, s);
-        const unsigned mn = __ballot_sync(kFull, accf && isnew);
-        const unsigned mo = __ballot_sync(kFull, accf && !isnew);
-        if (accf && isnew) st.cand_new[(size_t)u * st.cap + __popc(mn & lanemask_lt())] = (int)v;
-        if (accf && !isnew) st.cand_old[(size_t)u * st.cap + __popc(mo & lanemask_lt())] = (int)v;
-        if (lane == 0) {
-            st.fwd_new[u] = __popc(mn);
-            st.fwd_old[u] = __popc(mo);
+        // entry lane + 32 h of u's list
+        uint64_t key[KW];
+        bool isnew[KW];
+        uint32_t cnew = 0;
+#pragma unroll
+        for (int h = 0; h < KW; ++h) {
+            const bool valid = (int)lane + 32 * h < K;
+            key[h] = valid ? st.keys[(size_t)u * K + lane + 32 * h] : kKeyEmpty;
+            isnew[h] = valid && (key[h] & kFlagNew);
+            cnew += __popc(__ballot_sync(kFull, isnew[h]));
         }
-        if (valid) {
-            const int rc = isnew ? st.rev_new[v] : st.rev_old[v];
-            if (accept(hash_uj(rbase, ul, lane), (uint32_t)rc, s)) {
-                int slot = atomicAdd(isnew ? &st.fill_new[v] : &st.fill_old[v], 1);
-                if (slot < st.R)
-                    (isnew ? st.cand_new : st.cand_old)[(size_t)v * st.cap + K + slot] = (int)u;
-                else
-                    ++overflow;
+        const uint32_t cold = (uint32_t)K - cnew;
+        uint32_t nbase = 0, obase = 0;  // accepted new / old entries of the halves before
+#pragma unroll
+        for (int h = 0; h < KW; ++h) {
+            const int k = (int)lane + 32 * h;
+            const bool valid = k < K;
+            const uint32_t v = key_id(key[h]);
+            bool accf = false;
+            if (valid) accf = accept(hash_uj(fbase, ul, (uint64_t)k), isnew[h] ? cnew : cold, s);
+            const unsigned mn = __ballot_sync(kFull, accf && isnew[h]);
+            const unsigned mo = __ballot_sync(kFull, accf && !isnew[h]);
+            if (accf && isnew[h]) st.cand_new[(size_t)u * st.cap + nbase + __popc(mn & lanemask_lt())] = (int)v;
+            if (accf && !isnew[h]) st.cand_old[(size_t)u * st.cap + obase + __popc(mo & lanemask_lt())] = (int)v;
+            nbase += __popc(mn);
+            obase += __popc(mo);
+            if (valid) {
+                const int rc = isnew[h] ? st.rev_new[v] : st.rev_old[v];
+                if (accept(hash_uj(rbase, ul, (uint64_t)k), (uint32_t)rc, s)) {
+                    int slot = atomicAdd(isnew[h] ? &st.fill_new[v] : &st.fill_old[v], 1);
+                    if (slot < st.R)
+                        (isnew[h] ? st.cand_new : st.cand_old)[(size_t)v * st.cap + K + slot] = (int)u;
+                    else
+                        ++overflow;
+                }
+                uint64_t nk = key[h] & ~(uint64_t)kFlagIns;
+                if (accf && isnew[h]) nk &= ~(uint64_t)kFlagNew;
+                if (nk != key[h]) st.keys[(size_t)u * K + k] = nk;
             }
-            uint64_t nk = key & ~(uint64_t)kFlagIns;
-            if (accf && isnew) nk &= ~(uint64_t)kFlagNew;
-            if (nk != key) st.keys[(size_t)u * K + lane] = nk;
+        }
+        if (lane == 0) {
+            st.fwd_new[u] = (int)nbase;
+            st.fwd_old[u] = (int)obase;
         }
     }
     overflow = warp_sum(overflow);
@@ -343,9 +419,14 @@ __global__ void __launch_bounds__(kBlock) sample_kernel(DevState st, int li, uin
 }
 
 cudaError_t launch_sample(const DevState &st, int li, int it, uint64_t seed, cudaStream_t s) {
-    int grid = grid_for((const void *)sample_kernel, kBlock, 0);
-    sample_kernel<<<grid, kBlock, 0, s>>>(st, li, hash_base(seed, kStreamFwd, (uint32_t)it),
-                                          hash_base(seed, kStreamRev, (uint32_t)it));
+    const uint64_t fb = hash_base(seed, kStreamFwd, (uint32_t)it), rb = hash_base(seed, kStreamRev, (uint32_t)it);
+    if (st.K > kLaneK) {
+        int grid = grid_for((const void *)sample_kernel<2>, kBlock, 0);
+        sample_kernel<2><<<grid, kBlock, 0, s>>>(st, li, fb, rb);
+        return cudaGetLastError();
+    }
+    int grid = grid_for((const void *)sample_kernel<1>, kBlock, 0);
+    sample_kernel<1><<<grid, kBlock, 0, s>>>(st, li, fb, rb);
     return cudaGetLastError();
 }
 
@@ -502,6 +583,7 @@ cudaError_t launch_heap_sample(const DevState &st, int li, int it, uint64_t seed
 // (the value of sigma(x) before the first swap).  One warp runs the whole
 // chain: lanes hold the K list entries and test their spots in parallel; the
 // first qualifying lane is found with a ballot.
+template <int KW>
 __global__ void __launch_bounds__(32) greedy_reorder_kernel(const uint64_t *__restrict__ keys, int64_t n, int K,
                                                             int reading_b, int32_t *sigma, int32_t *sigma_inv) {
     const unsigned lane = lane_id();
@@ -513,21 +595,32 @@ __global__ void __launch_bounds__(32) greedy_reorder_kernel(const uint64_t *__re
     int32_t node = 0;  // node on spot i (reading A); kept in a register across steps
     for (int64_t i = 0; i + 1 < n; ++i) {
         const int64_t who = reading_b ? i : node;
-        int32_t x = -1;
-        int64_t p = -1;
-        if ((int)lane < K) {
-            x = (int32_t)key_id(__ldg(keys + (size_t)who * K + lane));
-            p = ((volatile int32_t *)sigma)[x];
+        // the first entry (in list order) whose node sits on a later spot
+        int32_t xs = -1;
+        int64_t ps = -1;
+        bool found = false;
+#pragma unroll
+        for (int h = 0; h < KW && !found; ++h) {
+            const int k = (int)lane + 32 * h;
+            int32_t x = -1;
+            int64_t p = -1;
+            if (k < K) {
+                x = (int32_t)key_id(__ldg(keys + (size_t)who * K + k));
+                p = ((volatile int32_t *)sigma)[x];
+            }
+            const unsigned later = __ballot_sync(kFull, k < K && p >= i + 1);
+            if (later) {
+                const int src = __ffs(later) - 1;
+                xs = __shfl_sync(kFull, x, src);
+                ps = __shfl_sync(kFull, p, src);
+                found = true;
+            }
         }
-        const unsigned later = __ballot_sync(kFull, (int)lane < K && p >= i + 1);
         int32_t next_node;
         const int32_t held = ((volatile int32_t *)sigma_inv)[i + 1];
-        if (later == 0) {
+        if (!found) {
             next_node = held;
         } else {
-            const int src = __ffs(later) - 1;
-            const int32_t xs = __shfl_sync(kFull, x, src);
-            const int64_t ps = __shfl_sync(kFull, p, src);
             if (ps == i + 1) {
                 next_node = xs;
             } else {
@@ -547,13 +640,15 @@ __global__ void __launch_bounds__(32) greedy_reorder_kernel(const uint64_t *__re
 
 cudaError_t launch_greedy_reorder(const uint64_t *keys, int64_t n, int K, int reading_b, int32_t *sigma,
                                   int32_t *sigma_inv, cudaStream_t s) {
-    greedy_reorder_kernel<<<1, 32, 0, s>>>(keys, n, K, reading_b, sigma, sigma_inv);
+    if (K > kLaneK) greedy_reorder_kernel<2><<<1, 32, 0, s>>>(keys, n, K, reading_b, sigma, sigma_inv);
+    else greedy_reorder_kernel<1><<<1, 32, 0, s>>>(keys, n, K, reading_b, sigma, sigma_inv);
     return cudaGetLastError();
 }
 
 // Move node u to spot sigma(u) (Section 3.2, all at once): its padded row and
 // its list, ids renamed through sigma and re-sorted by (dist, new id).  The
 // total relabelling original -> spot is composed with sigma.
+template <int KW>
 __global__ void __launch_bounds__(kBlock) permute_kernel(DevState st, float *__restrict__ X_dst,
                                                          uint64_t *__restrict__ keys_dst,
                                                          const int32_t *__restrict__ sigma,
@@ -565,21 +660,34 @@ __global__ void __launch_bounds__(kBlock) permute_kernel(DevState st, float *__r
     for (long long u = gwarp(); u < st.n; u += nwarps()) {
         const int32_t p = sigma[u];
         for (int c = lane; c < st.nv; c += 32) D4[(size_t)p * st.nv + c] = X4[(size_t)u * st.nv + c];
-        uint64_t key = kKeyEmpty;
-        if ((int)lane < K) {
-            uint64_t k0 = st.keys[(size_t)u * K + lane];
-            key = (k0 & 0xFFFFFFFF00000003ull) | ((uint64_t)(uint32_t)sigma[key_id(k0)] << 2);
+        uint64_t key[KW];
+#pragma unroll
+        for (int h = 0; h < KW; ++h) {
+            const int k = (int)lane + 32 * h;
+            key[h] = kKeyEmpty;
+            if (k < K) {
+                const uint64_t k0 = st.keys[(size_t)u * K + k];
+                key[h] = (k0 & 0xFFFFFFFF00000003ull) | ((uint64_t)(uint32_t)sigma[key_id(k0)] << 2);
+            }
         }
-        key = warp_sort_u64(key);
-        if ((int)lane < K) keys_dst[(size_t)p * K + lane] = key;
+        if constexpr (KW == 2) warp_sort_u64x2(key[0], key[KW - 1]);
+        else key[0] = warp_sort_u64(key[0]);
+#pragma unroll
+        for (int h = 0; h < KW; ++h)
+            if ((int)lane + 32 * h < K) keys_dst[(size_t)p * K + lane + 32 * h] = key[h];
         if (lane == 0) total_perm[u] = sigma[total_perm[u]];
     }
 }
 
 cudaError_t launch_permute(const DevState &src, float *X_dst, uint64_t *keys_dst, const int32_t *sigma,
                            int32_t *total_perm, cudaStream_t s) {
-    int grid = grid_for((const void *)permute_kernel, kBlock, 0);
-    permute_kernel<<<grid, kBlock, 0, s>>>(src, X_dst, keys_dst, sigma, total_perm);
+    if (src.K > kLaneK) {
+        int grid = grid_for((const void *)permute_kernel<2>, kBlock, 0);
+        permute_kernel<2><<<grid, kBlock, 0, s>>>(src, X_dst, keys_dst, sigma, total_perm);
+        return cudaGetLastError();
+    }
+    int grid = grid_for((const void *)permute_kernel<1>, kBlock, 0);
+    permute_kernel<1><<<grid, kBlock, 0, s>>>(src, X_dst, keys_dst, sigma, total_perm);
     return cudaGetLastError();
 }
 
@@ -631,7 +739,7 @@ cudaError_t launch_invert(const int32_t *perm, int64_t n, int32_t *inv, cudaStre
 // their pair (init and every join compute it the same way, and both orders of
 // a pair agree bit for bit), so they are taken as they are; the approximate
 // keys of the bf16 and FP8 forms are re-ranked with the canonical distance.
-template <bool kStaged>
+template <bool kStaged, int KW>
 __global__ void __launch_bounds__(kBlock) output_kernel(DevState st, const int32_t *__restrict__ total_perm,
                                                         const int32_t *__restrict__ total_inv,
                                                         int32_t *__restrict__ ids, float *__restrict__ dists) {
@@ -641,38 +749,54 @@ __global__ void __launch_bounds__(kBlock) output_kernel(DevState st, const int32
     const float4 *X4 = reinterpret_cast<const float4 *>(st.X);
     for (long long u = gwarp(); u < st.n; u += nwarps()) {
         const int64_t p = total_perm ? total_perm[u] : u;
-        uint64_t key = kKeyEmpty;
-        const uint64_t lk = (int)lane < K ? st.keys[(size_t)p * K + lane] : kKeyEmpty;
-        const uint32_t v = (int)lane < K ? key_id(lk) : (uint32_t)p;
-        float dd;
-        if (!st.bf16) dd = (int)lane < K ? key_dist(lk) : 0.f;
-        else if (kStaged) dd = warp_staged_dist(X4, st.nv, p, v, K, stage_sm + (threadIdx.x >> 5) * 33 * (st.nv | 1));
-        else dd = (int)lane < K ? l2sq_rows(X4 + (size_t)p * st.nv, X4 + (size_t)v * st.nv, st.nv) : 0.f;
-        if ((int)lane < K) {
-            uint32_t vo = total_inv ? (uint32_t)total_inv[v] : v;
-            if (st.ds) vo -= (uint32_t)st.ds_off[st.ds[u]];  // batched: ids local to the data set
-            key = make_key(dd, vo, 0);
+        uint64_t key[KW];
+#pragma unroll
+        for (int h = 0; h < KW; ++h) {
+            const int k = (int)lane + 32 * h;
+            const int cnt = K - 32 * h < 32 ? K - 32 * h : 32;
+            key[h] = kKeyEmpty;
+            const uint64_t lk = k < K ? st.keys[(size_t)p * K + k] : kKeyEmpty;
+            const uint32_t v = k < K ? key_id(lk) : (uint32_t)p;
+            float dd;
+            if (!st.bf16) dd = k < K ? key_dist(lk) : 0.f;
+            else if (kStaged) dd = warp_staged_dist(X4, st.nv, p, v, cnt, stage_sm + (threadIdx.x >> 5) * 33 * (st.nv | 1));
+            else dd = k < K ? l2sq_rows(X4 + (size_t)p * st.nv, X4 + (size_t)v * st.nv, st.nv) : 0.f;
+            if (k < K) {
+                uint32_t vo = total_inv ? (uint32_t)total_inv[v] : v;
+                if (st.ds) vo -= (uint32_t)st.ds_off[st.ds[u]];  // batched: ids local to the data set
+                key[h] = make_key(dd, vo, 0);
+            }
         }
-        key = warp_sort_u64(key);
-        if ((int)lane < K) {
-            ids[(size_t)u * K + lane] = (int32_t)key_id(key);
-            dists[(size_t)u * K + lane] = key_dist(key);
+        if constexpr (KW == 2) warp_sort_u64x2(key[0], key[KW - 1]);
+        else key[0] = warp_sort_u64(key[0]);
+#pragma unroll
+        for (int h = 0; h < KW; ++h) {
+            const int k = (int)lane + 32 * h;
+            if (k < K) {
+                ids[(size_t)u * K + k] = (int32_t)key_id(key[h]);
+                dists[(size_t)u * K + k] = key_dist(key[h]);
+            }
         }
     }
 }
 
 cudaError_t launch_output(const DevState &st, const int32_t *total_perm, const int32_t *total_inv,
                           int32_t *ids, float *dists, cudaStream_t s) {
-    if (st.bf16 && st.nv >= kStageMinNv && st.nv <= kStageMaxNv) {
-        const size_t dyn = stage_smem_bytes(st.nv);
-        cudaError_t e = smem_opt_in((const void *)output_kernel<true>, dyn);
-        if (e != cudaSuccess) return e;
-        const int grid = grid_for((const void *)output_kernel<true>, kStageWarps * 32, dyn);
-        output_kernel<true><<<grid, kStageWarps * 32, dyn, s>>>(st, total_perm, total_inv, ids, dists);
+    if (st.K > kLaneK) {  // float32 keys only: no re-rank
+        int grid = grid_for((const void *)output_kernel<false, 2>, kBlock, 0);
+        output_kernel<false, 2><<<grid, kBlock, 0, s>>>(st, total_perm, total_inv, ids, dists);
         return cudaGetLastError();
     }
-    int grid = grid_for((const void *)output_kernel<false>, kBlock, 0);
-    output_kernel<false><<<grid, kBlock, 0, s>>>(st, total_perm, total_inv, ids, dists);
+    if (st.bf16 && st.nv >= kStageMinNv && st.nv <= kStageMaxNv) {
+        const size_t dyn = stage_smem_bytes(st.nv);
+        cudaError_t e = smem_opt_in((const void *)output_kernel<true, 1>, dyn);
+        if (e != cudaSuccess) return e;
+        const int grid = grid_for((const void *)output_kernel<true, 1>, kStageWarps * 32, dyn);
+        output_kernel<true, 1><<<grid, kStageWarps * 32, dyn, s>>>(st, total_perm, total_inv, ids, dists);
+        return cudaGetLastError();
+    }
+    int grid = grid_for((const void *)output_kernel<false, 1>, kBlock, 0);
+    output_kernel<false, 1><<<grid, kBlock, 0, s>>>(st, total_perm, total_inv, ids, dists);
     return cudaGetLastError();
 }
 

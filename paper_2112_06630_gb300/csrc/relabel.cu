@@ -61,10 +61,10 @@ __global__ void __launch_bounds__(256) relabel_dist_kernel(RelabelState r) {
     const unsigned lane = lane_id();
     const float4 *X4 = reinterpret_cast<const float4 *>(r.X);
     for (long long u = rl_warp(); u < r.n; u += rl_warps()) {
-        if ((int)lane < r.K) {
-            const uint32_t v = key_id(r.keys[(size_t)u * r.K + lane]);
+        for (int k = (int)lane; k < r.K; k += 32) {
+            const uint32_t v = key_id(r.keys[(size_t)u * r.K + k]);
             const float d = l2sq_rows(X4 + (size_t)u * r.nv, X4 + (size_t)v * r.nv, r.nv);
-            r.dist[(size_t)u * r.K + lane] = __float_as_uint(d);
+            r.dist[(size_t)u * r.K + k] = __float_as_uint(d);
         }
     }
 }

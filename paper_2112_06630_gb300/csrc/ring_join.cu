@@ -352,6 +352,7 @@ __device__ __forceinline__ void warp_gram_fp8(const unsigned char *rows, uint32_
 }  // namespace
 
 // ------------------------------------------------------------ set_kernel --
+template <int kWide>
 __global__ void __launch_bounds__(kSetWarps * 32) set_kernel(DevState st, int li) {
     if (iteration_skipped(st, li)) return;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -361,16 +362,17 @@ __global__ void __launch_bounds__(kSetWarps * 32) set_kernel(DevState st, int li
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
     const int raw_max = ((2 * st.cap + 31) / 32) * 32;
-    int *wbase = reinterpret_cast<int *>(smem) + (size_t)warp * (raw_max + (1 << kHashBits) + kSetMax);
+    int *wbase = reinterpret_cast<int *>(smem) + (size_t)warp * (raw_max + (1 << hash_bits(st.cap)) + kSetMax);
     int *hset = wbase;
-    int *raw = hset + (1 << kHashBits);
+    int *raw = hset + (1 << hash_bits(st.cap));
     int *sid = raw + raw_max;
     long long w_candids = 0, w_setovf = 0;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long u = gw; u < st.n; u += nw) {
         int ns = 0, m = 0;
-        if (!node_skipped(st, u, li)) w_candids += warp_gather_candidates(st, u, raw, hset, sid, ns, m, w_setovf);
+        if (!node_skipped(st, u, li))
+            w_candids += warp_gather_candidates<kWide>(st, u, raw, hset, sid, ns, m, w_setovf);
         for (int i = lane; i < ns; i += 32) st.cset[(size_t)u * kSetMax + i] = sid[i];
         if (lane == 0) st.cmeta[u] = ns | (m << 8);
         __syncwarp();
@@ -821,7 +823,7 @@ bool ring_join_preferred(int bf16, int nv, int dpb) {
 
 size_t set_kernel_smem(int cap) {
     const int raw_max = ((2 * cap + 31) / 32) * 32;
-    return sizeof(int) * (size_t)kSetWarps * (raw_max + (1 << kHashBits) + kSetMax);
+    return sizeof(int) * (size_t)kSetWarps * (raw_max + (1 << hash_bits(cap)) + kSetMax);
 }
 
 namespace {
@@ -841,8 +843,15 @@ cudaError_t launch_ring_t(const DevState &st, int li, cudaStream_t s) {
 
 cudaError_t launch_set_kernel(const DevState &st, int li, cudaStream_t s) {
     const size_t dyn = set_kernel_smem(st.cap);
-    const int grid = grid_for((const void *)set_kernel, kSetWarps * 32, dyn);
-    set_kernel<<<grid, kSetWarps * 32, dyn, s>>>(st, li);
+    // the narrow form (reverse capacity <= 96, 256-slot hash set) keeps the
+    // registers of the usual K <= 32 builds
+    if (st.R > 96 || hash_bits(st.cap) > kHashBits) {
+        const int grid = grid_for((const void *)set_kernel<1>, kSetWarps * 32, dyn);
+        set_kernel<1><<<grid, kSetWarps * 32, dyn, s>>>(st, li);
+        return cudaGetLastError();
+    }
+    const int grid = grid_for((const void *)set_kernel<0>, kSetWarps * 32, dyn);
+    set_kernel<0><<<grid, kSetWarps * 32, dyn, s>>>(st, li);
     return cudaGetLastError();
 }
 

@@ -39,12 +39,12 @@ constexpr int kItemsPerThread = 2;           // (new row, 4 columns) items per t
 constexpr int kChunkB = 64;                  // bf16 per row chunk
 constexpr int kStrideB = kChunkB + 8;        // 144-byte rows for ldmatrix
 constexpr int kDStride = kSetMax + 1;
-constexpr int kRawMax = 256;                 // >= 2 * (K + R) for K <= 32, s <= 32
+constexpr int kRawMax = 416;                 // >= 2 * (K + R) for K <= 64, s <= 64
 
 struct TileSmem {
     int sid[kSetMax];
     int raw[kRawMax];
-    int hset[1 << kHashBits];
+    int hset[1 << kHashBitsMax];
     uint64_t swk[kSetMax];
     unsigned long long mask[kSetMax];
     float nrm[kSetMax];
@@ -277,13 +277,13 @@ __global__ void __launch_bounds__(kTileThreads) tile_join_kernel(DevState st, in
             uint64_t *Lsnap = reinterpret_cast<uint64_t *>(stage_mem);  // the row stage is free now
             for (int e = tid; e < ns * K; e += kTileThreads) {
                 const int t = e / K, k = e - t * K;
-                if (sm.mask[t]) Lsnap[t * (kMaxK + 1) + k] = __ldcg(st.keys + (size_t)sm.sid[t] * K + k);
+                if (sm.mask[t]) Lsnap[t * (K + 1) + k] = __ldcg(st.keys + (size_t)sm.sid[t] * K + k);
             }
             __syncthreads();
             for (int t = tid; t < ns; t += kTileThreads) {
                 unsigned long long mt = sm.mask[t];
                 if (!mt) continue;
-                const uint64_t *Lt = Lsnap + t * (kMaxK + 1);
+                const uint64_t *Lt = Lsnap + t * (K + 1);
                 const uint64_t worst = Lt[K - 1];
                 for (unsigned long long mm = mt; mm; mm &= mm - 1) {
                     const int j = __ffsll((long long)mm) - 1;
@@ -399,7 +399,7 @@ template <bool kBF16>
 cudaError_t launch_tile_t(const DevState &st, int li, cudaStream_t s) {
     // two row-chunk buffers, later reused for the targets' list snapshots
     size_t dyn = kBF16 ? 2ull * kSetMax * kStrideB * sizeof(uint16_t) : 2ull * kSetMax * kStrideV * 16;
-    dyn = std::max(dyn, (size_t)kSetMax * (kMaxK + 1) * sizeof(uint64_t));
+    dyn = std::max(dyn, (size_t)kSetMax * (st.K + 1) * sizeof(uint64_t));
     auto kern = tile_join_kernel<kBF16>;
     cudaError_t e = smem_opt_in((const void *)kern, dyn);
     if (e != cudaSuccess) return e;

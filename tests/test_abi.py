@@ -67,11 +67,23 @@ def test_invalid_arguments_rejected_before_any_device_work(lib, n, d, K, rho, de
     assert rc == -1
 
 
-def test_k_above_32_unsupported(lib):
+def test_k_above_64_unsupported(lib):
+    """K <= 64 is built (two keys per lane above 32); K = 65 is refused, and
+    so are K > 32 with the low-precision and heap flags, before any device
+    work."""
+    import paper_2112_06630_gb300 as knng
     x = np.zeros((100, 4), np.float32)
-    ids = np.zeros((100, 40), np.int32)
-    dists = np.zeros((100, 40), np.float32)
-    assert lib.knng_build(x.ctypes.data, 100, 4, 40, 0.5, 0.0, 5, 0, ids.ctypes.data, dists.ctypes.data) == -5
+    ids = np.zeros((100, 65), np.int32)
+    dists = np.zeros((100, 65), np.float32)
+    assert lib.knng_build(x.ctypes.data, 100, 4, 65, 0.5, 0.0, 5, 0, ids.ctypes.data, dists.ctypes.data) == -5
+    for flag in (knng.FLAG_BF16, knng.FLAG_FP8, knng.FLAG_HEAP_SAMPLING):
+        assert lib.knng_build_ex(x.ctypes.data, 100, 4, 40, 0.5, 0.0, 5, 0, flag, None, ids.ctypes.data,
+                                 dists.ctypes.data, None) == -5
+    fn = lib.knng_bruteforce_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert fn(x.ctypes.data, 100, 4, 40, None, 0, ids.ctypes.data, dists.ctypes.data, None) == -5
 
 
 def test_null_pointers_rejected(lib):
@@ -136,7 +148,7 @@ def test_descriptor_layouts_match_the_binding(tmp_path):
 @pytest.mark.parametrize("field,value,code", [
     ("rho", 0.0, -1), ("rho", 1.5, -1), ("delta", -1.0, -1), ("max_iters", -1, -1), ("K", 0, -1),
     ("K", 10, -1),     # K > n - 1
-    ("d", 0, -1), ("K", 40, -5),
+    ("d", 0, -1), ("K", 65, -5),
 ])
 def test_batched_ex_rejects_any_bad_descriptor_before_device_work(lib, field, value, code):
     """knng_build_batched_ex checks every descriptor before any work: one bad

@@ -48,7 +48,7 @@ def assert_ids_up_to_ties(gi, gd, oi, od, rtol=1e-5):
 # ------------------------------------------------------------ brute force ----
 
 @pytest.mark.parametrize("n,d,K", [(2000, 8, 10), (1037, 5, 7), (700, 33, 16), (513, 16, 32), (300, 130, 20),
-                                   (2, 3, 1), (33, 4, 32)])
+                                   (2, 3, 1), (33, 4, 32), (700, 6, 48), (130, 3, 64), (65, 33, 64)])
 def test_bruteforce_matches_oracle(n, d, K):
     x = workloads.uniform(n, d, seed=n + d)
     gi, gd = knng.knng_bruteforce(_cuda(x), K)
@@ -136,7 +136,8 @@ def test_bruteforce_duplicate_points():
 
 # ------------------------------------------------------------ random init ----
 
-@pytest.mark.parametrize("n,d,K", [(3001, 8, 10), (500, 3, 20), (33, 5, 32), (2, 1, 1)])
+@pytest.mark.parametrize("n,d,K", [(3001, 8, 10), (500, 3, 20), (33, 5, 32), (2, 1, 1), (3000, 8, 48), (700, 5, 64),
+                                   (65, 4, 64), (900, 70, 40)])
 def test_init_matches_oracle_exactly(n, d, K):
     x = _int_data(n, d, 16, seed=K)
     with knng.Context(_cuda(x), K, rho=0.5, seed=7) as c:
@@ -160,6 +161,9 @@ CASES = [
     (400, 600, 12, 0.5, 3),     # block-per-node tile kernel (rows > 64 floats)
     (700, 65, 32, 0.3, 4),      # tile kernel, ragged last 64-float chunk
     (1500, 100, 20, 0.5, 3),    # tile kernel, two passes of new rows possible
+    (2000, 8, 40, 0.25, 16),    # two list keys per lane (K > 32)
+    (1500, 12, 64, 0.15, 8),    # K = 64
+    (800, 140, 48, 0.2, 3),     # K = 48 through the pipelined kernel
 ]
 
 
@@ -198,6 +202,8 @@ PATH_CASES = [
     (2000, 200, 20, 1.0, 3, False),   # two column blocks of the pipelined kernel, up to 64 candidates
     (1500, 33, 16, 0.5, 4, False),    # 9 float4 per row: the narrowest pipelined row
     (3000, 256, 24, 0.5, 3, False),   # the widest pipelined row (64 float4)
+    (1200, 100, 48, 0.2, 3, False),   # K = 48: two list keys per lane, 48-entry list snapshots
+    (900, 300, 64, 0.15, 3, False),   # K = 64
 ]
 PATH_IDS = {"warp": 0, "tile": 1, "ring": 2, "pipe": 3, "pipe8": 4}
 
@@ -387,9 +393,9 @@ def test_alg1_golden_on_gpu():
             assert c.permutation().tolist() == g[f"sigma_reading_{rd}"]
 
 
-@pytest.mark.parametrize("reading_b", [False, True])
-def test_alg1_matches_oracle(reading_b):
-    n, K = 6000, 10
+@pytest.mark.parametrize("reading_b,K", [(False, 10), (True, 10), (False, 40), (True, 64)])
+def test_alg1_matches_oracle(reading_b, K):
+    n = 6000
     x = _int_data(n, 6, 20, seed=9)
     ei, _ = oracle.bruteforce(x, K)
     flags = knng.FLAG_REORDER | (knng.FLAG_REORDER_B if reading_b else 0)
@@ -422,6 +428,63 @@ def test_build_plain_matches_oracle_bit_exact():
     oi, od, ost = oracle.build_knng(x, K, 0.5, 0.001, 12, seed=9)
     assert st["iterations"] == ost["iters"] and st["dist_evals"] == ost["evals"]
     assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+@pytest.mark.parametrize("pool", ["1", "40"])
+def test_wide_lists_bucket_overflow_and_builds_match_oracle(pool, monkeypatch):
+    """K = 64 (two keys per lane): a tiny proposal pool drives proposals
+    through poisoned runs and locked insertions into 64-entry lists, one
+    iteration bit-exact against the oracle; then a whole K = 48 build and a
+    relabelled K = 40 build equal the oracle's."""
+    monkeypatch.setenv("KNNG_TEST_BUCKET_POOL_CHUNKS", pool)
+    n, d, K, rho, hi = 1500, 3, 64, 0.15, 8
+    x = _int_data(n, d, hi, seed=n)
+    ids0, new0 = workloads.random_graph(n, K, seed=n + 1, p_new=0.6)
+    with knng.Context(_cuda(x), K, rho=rho, seed=11, graph=(ids0, new0), iter=0) as c:
+        conv, ch = c.iterate()
+        gi, gd, gf = c.state()
+        stats = c.stats()
+    st = oracle.State(x, K, rho, seed=11)
+    st.init_graph(ids0, new0, 0)
+    r = st.iterate()
+    assert stats["bucket_overflow"] > 0 and stats["lock_timeouts"] == 0 and stats["set_overflow"] == 0
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    assert ch == r["changes"]
+    monkeypatch.delenv("KNNG_TEST_BUCKET_POOL_CHUNKS")
+    x = _int_data(3000, 6, 9, seed=3)
+    gi, gd, st = knng.knng_build(_cuda(x), 48, rho=0.2, delta=0.001, max_iters=10, seed=9)
+    oi, od, ost = oracle.build_knng(x, 48, 0.2, 0.001, 10, seed=9)
+    assert st["iterations"] == ost["iters"] and st["set_overflow"] == 0
+    assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
+    x = _int_data(2500, 8, 12, seed=21)
+    gi, gd, st = knng.knng_build(_cuda(x), 40, rho=0.25, delta=0.002, max_iters=8, seed=4, flags=knng.FLAG_REORDER)
+    oi, od, ost = oracle.build_knng(x, 40, 0.25, 0.002, 8, seed=4, reorder=1)
+    assert st["reordered"] == 1 and st["iterations"] == ost["iters"]
+    assert (gi.cpu().numpy() == oi).all() and (gd.cpu().numpy() == od).all()
+
+
+def test_wide_lists_real_data_recall_batched_and_refusals():
+    """K = 64 on real-valued clustered data: list invariants and every
+    distance within 1e-4 of its float64 recomputation, recall within 0.005 of
+    the oracle's build; a batched K = 48 build equals the single builds; the
+    flags that keep one key per lane refuse K > 32."""
+    x = workloads.gaussian_mixture(6000, 24, 15, seed=8)
+    gi, gd, st = knng.knng_build(_cuda(x), 64, 0.3, 0.001, 10, seed=2)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    assert metrics.check_graph(x, gi, gd) == []
+    rows = np.arange(0, 6000, 7)
+    ei, _ = oracle.bruteforce(x, 64, rows)
+    oi, _, _ = oracle.build_knng_mt(x, 64, 0.3, 0.001, 10, seed=2)
+    assert abs(metrics.recall(x, gi, ei, rows) - metrics.recall(x, oi, ei, rows)) <= 0.005
+    sets = [workloads.gaussian_mixture(n, d, 6, seed=n) for n, d in [(2000, 24), (1500, 70), (2500, 24)]]
+    outs, _ = knng.knng_build_batched([_cuda(v) for v in sets], 48, 0.25, 0.001, 8, seed=5)
+    for v, (bi, bd) in zip(sets, outs):
+        si, sd, _ = knng.knng_build(_cuda(v), 48, 0.25, 0.001, 8, seed=5)
+        assert torch.equal(bi, si) and torch.equal(bd, sd)
+    for flag in (knng.FLAG_BF16, knng.FLAG_FP8, knng.FLAG_HEAP_SAMPLING):
+        with pytest.raises(knng.KnngError):
+            knng.knng_build(_cuda(sets[1]), 40, 0.5, 0.001, 4, seed=0, flags=flag)
 
 
 # ------------------------------------------------------- whole builds ----
