@@ -98,6 +98,7 @@ struct Acc2 {
 
 __device__ __forceinline__ float l2sq_rows(const float4 *__restrict__ a, const float4 *__restrict__ b, int nv) {
     Acc2 acc;
+#pragma unroll 8
     for (int v = 0; v < nv; ++v) acc.add(a[v], b[v]);
     return acc.sum();
 }

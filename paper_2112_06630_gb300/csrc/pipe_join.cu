@@ -166,6 +166,9 @@ __device__ __forceinline__ void pipe_block(const unsigned char *rows, const Pipe
         for (int r = 0; r < RB; ++r) pr[r] = reinterpret_cast<const float4 *>(base + (uint32_t)ri[r] * st);
 #pragma unroll
         for (int q = 0; q < CB; ++q) pc[q] = reinterpret_cast<const float4 *>(base + (uint32_t)cj[q] * st);
+        // unrolled by eight (measured on the 1M x 128 build: 150.1 -> 149.0 ms;
+        // by four no change, by sixteen or more slower)
+#pragma unroll 8
         for (int v = 0; v < units; ++v) {
             float4 x[RB], y[CB];
 #pragma unroll

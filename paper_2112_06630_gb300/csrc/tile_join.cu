@@ -122,6 +122,9 @@ __device__ void tile_dist_f32(TileSmem &sm, float4 *stage, const float4 *X4, int
                 if (ii[w] < 0) continue;
                 const float4 *ri = b + ii[w] * kStrideV;
                 const float4 *rj = b + jj[w] * kStrideV;
+                // unrolled (a chunk is at most 8 units): MNIST-shaped float32
+                // build 35.5 -> 32.9 ms
+#pragma unroll 8
                 for (int v = 0; v < vc; ++v) {
                     const float4 a = ri[v];
 #pragma unroll
