@@ -62,8 +62,9 @@ __device__ __forceinline__ bool warp_insert(uint64_t &Lk, uint64_t x, int K) {
 }
 
 // Reverse part raw[b, b + cnt) (cnt <= 32 H; reverse capacities are at most
-// 2 * 32 + 8 = 72 for K <= 32 and 2 * 64 + 8 = 136 above) put in a fixed order: ascending by (id - base) * 0x9E3779B1 mod
-// 2^32, a bijection of the ids local to the data set (base: its first node),
+// 2 * 32 + 8 = 72 for K <= 32 and 2 * 64 + 8 = 136 above) put in a fixed
+// order: ascending by (id - base) * 0x9E3779B1 mod 2^32, a bijection of the
+// ids local to the data set (base: its first node),
 // so the order is canonical, the same in a batched build, and not tied to id
 // size.  The ids of one reverse part are distinct (a node lists an id once).
 template <int H>

@@ -528,6 +528,49 @@ def test_complete_graph_k_equals_n_minus_1():
     assert_ids_up_to_ties(gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
 
 
+@pytest.mark.parametrize("n,K", [(65, 64), (34, 33), (50, 40)])
+def test_complete_graph_wide_lists(n, K):
+    """K = n - 1 with two keys per lane: the random init already lists
+    every other point, so the result is the exact K-NNG."""
+    x = workloads.uniform(n, 5, seed=n)
+    gi, gd, st = knng.knng_build(_cuda(x), K, 1.0, 0.0, 2, seed=1)
+    oi, od = oracle.bruteforce(x, K)
+    assert_ids_up_to_ties(gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+
+
+def test_wide_lists_k33_iteration_relabels_and_mixed_batch():
+    """K = 33 (a single entry in the second half of each lane pair): one
+    iteration bit-exact against the oracle; K = 64 lists through the parallel
+    relabelling keep a valid graph in the caller's labels; a batched call
+    with K = 20 and K = 50 data sets equals their single builds."""
+    n, d, K, rho = 1500, 6, 33, 0.3
+    x = _int_data(n, d, 8, seed=33)
+    ids0, new0 = workloads.random_graph(n, K, seed=34, p_new=0.6)
+    with knng.Context(_cuda(x), K, rho=rho, seed=5, graph=(ids0, new0), iter=0) as c:
+        conv, ch = c.iterate()
+        gi, gd, gf = c.state()
+        stats = c.stats()
+    st = oracle.State(x, K, rho, seed=5)
+    st.init_graph(ids0, new0, 0)
+    r = st.iterate()
+    assert stats["set_overflow"] == 0
+    oi, od, of = st.state()
+    assert (gi == oi).all() and (gd == od).all() and (gf == of).all()
+    assert ch == r["changes"]
+    y = workloads.gaussian_mixture(5000, 12, 10, seed=2)
+    flags = knng.FLAG_REORDER | knng.FLAG_REORDER_PARALLEL
+    ri, rd, rst = knng.knng_build(_cuda(y), 64, 0.25, 0.001, 8, seed=3, flags=flags)
+    assert rst["reordered"] == 1
+    assert metrics.check_graph(y, ri.cpu().numpy(), rd.cpu().numpy()) == []
+    sets = [workloads.gaussian_mixture(m, 24, 6, seed=m) for m in (1800, 2600)]
+    items = [dict(data=_cuda(sets[0]), K=20, rho=0.5, delta=0.001, max_iters=8, seed=1),
+             dict(data=_cuda(sets[1]), K=50, rho=0.25, delta=0.001, max_iters=8, seed=1)]
+    outs, _ = knng.knng_build_batched_ex(items)
+    for it, (bi, bd) in zip(items, outs):
+        si, sd, _ = knng.knng_build(it["data"], it["K"], it["rho"], it["delta"], it["max_iters"], seed=it["seed"])
+        assert torch.equal(bi, si) and torch.equal(bd, sd)
+
+
 def test_all_points_equal():
     x = np.ones((500, 8), np.float32)
     gi, gd, st = knng.knng_build(_cuda(x), 10, 0.5, 0.0, 3, seed=0)
