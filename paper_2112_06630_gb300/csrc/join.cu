@@ -402,6 +402,9 @@ __device__ __forceinline__ int merge_batch(uint64_t &Lk, uint64_t x, int K, bool
     if (bf16) {
         listed = !bf16_resolve_ids(Lk, x, K, ins);
     } else {
+        // lower bound of (dist, id) among the entries: xo has its flag bits
+        // clear and a (dist, id) is listed at most once, so comparing whole
+        // keys with xo decides as comparing them without their flags
         const uint64_t xo = key_order(x);
         int lo = 0, hi = K - 1;
 #pragma unroll
@@ -409,7 +412,7 @@ __device__ __forceinline__ int merge_batch(uint64_t &Lk, uint64_t x, int K, bool
             const int mid = (lo + hi) >> 1;
             const uint64_t lm = __shfl_sync(kFull, Lk, mid);
             if (lo < hi) {
-                if (key_order(lm) < xo) lo = mid + 1;
+                if (lm < xo) lo = mid + 1;
                 else hi = mid;
             }
         }
@@ -436,7 +439,7 @@ __device__ __forceinline__ int merge_batch_wide(WList &L, uint64_t x, int K) {
         const int mid = (lo + hi) >> 1;
         const uint64_t a = __shfl_sync(kFull, L.lo, mid & 31), b = __shfl_sync(kFull, L.hi, mid & 31);
         if (lo < hi) {
-            if (key_order(mid < 32 ? a : b) < xo) lo = mid + 1;
+            if ((mid < 32 ? a : b) < xo) lo = mid + 1;  // as in merge_batch: flags need no mask
             else hi = mid;
         }
     }
