@@ -56,12 +56,16 @@ RECALL_ROWS = 2000
 RECALL99 = {
     "mixture_n1m_d128": (0.7, 0.001, 12),
     "clustered_n100k_d16": (0.55, 0.001, 15),
+    "mnist_like_n70k_d784": (0.6, 0.001, 15),
+    "audio_like_n54k_d192": (0.7, 0.001, 15),
 }
 # ladders reported beside the timed point: (rho, delta, max_iters)
 LADDER = {
     "mixture_n1m_d128": [(0.3, 0.001, 12), (0.3, 0.0, 30), (0.5, 0.001, 12), (0.6, 0.001, 12),
                          (0.7, 0.001, 12), (1.0, 0.001, 12)],
     "clustered_n100k_d16": [(0.5, 0.001, 15), (0.55, 0.001, 15), (0.6, 0.001, 15)],
+    "mnist_like_n70k_d784": [(0.5, 0.001, 15), (0.6, 0.001, 15), (0.7, 0.001, 15), (1.0, 0.001, 15)],
+    "audio_like_n54k_d192": [(0.5, 0.001, 15), (0.6, 0.001, 15), (0.7, 0.001, 15), (0.8, 0.001, 15)],
 }
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_recall.json")
 
