@@ -274,20 +274,23 @@ __device__ __forceinline__ void warp_gram_bf16(const unsigned char *rows, uint32
             asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                          : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
                          : "r"(abase + kk * 32));
+            // all B fragments of the k-step first, then the MMAs: the loads
+            // overlap instead of each MMA waiting on its own load
+            uint32_t b0[8], b1[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (q < ntiles) {
-                    uint32_t b0, b1;
+            for (int q = 0; q < 8; ++q)
+                if (q < ntiles)
                     asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-                                 : "=r"(b0), "=r"(b1)
+                                 : "=r"(b0[q]), "=r"(b1[q])
                                  : "r"(bbase[q] + kk * 32));
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < ntiles)
                     asm volatile(
                         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
                         "{%8,%9}, {%0,%1,%2,%3};\n"
                         : "+f"(acc[q][0]), "+f"(acc[q][1]), "+f"(acc[q][2]), "+f"(acc[q][3])
-                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-                }
-            }
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0[q]), "r"(b1[q]));
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -325,20 +328,22 @@ __device__ __forceinline__ void warp_gram_fp8(const unsigned char *rows, uint32_
             asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                          : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
                          : "r"(abase + kk * 32));
+            // all B fragments of the k-step first, then the MMAs (as in bf16)
+            uint32_t b0[8], b1[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (q < ntiles) {
-                    uint32_t b0, b1;
+            for (int q = 0; q < 8; ++q)
+                if (q < ntiles)
                     asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-                                 : "=r"(b0), "=r"(b1)
+                                 : "=r"(b0[q]), "=r"(b1[q])
                                  : "r"(bbase[q] + kk * 32));
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < ntiles)
                     asm volatile(
                         "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
                         "{%8,%9}, {%0,%1,%2,%3};\n"
                         : "+f"(acc[q][0]), "+f"(acc[q][1]), "+f"(acc[q][2]), "+f"(acc[q][3])
-                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-                }
-            }
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0[q]), "r"(b1[q]));
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
