@@ -174,19 +174,23 @@ __device__ void tile_dist_b16(TileSmem &sm, uint16_t *stage, const uint16_t *Xb,
             asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                          : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
                          : "r"(smem_u32(b + arow * kStrideB + ks * 16 + acol)));
+            // the B fragments first, then the MMAs (the loads overlap); column
+            // tiles past the set are skipped (warp-uniform)
+            uint32_t b0[4], b1[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if ((nt0 + q) * 8 >= ns) break;  // warp-uniform: columns past the set
-                uint32_t b0, b1;
-                asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-                             : "=r"(b0), "=r"(b1)
-                             : "r"(smem_u32(b + ((nt0 + q) * 8 + brow) * kStrideB + ks * 16 + bcol)));
-                asm volatile(
-                    "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                    "{%0,%1,%2,%3};\n"
-                    : "+f"(acc[q][0]), "+f"(acc[q][1]), "+f"(acc[q][2]), "+f"(acc[q][3])
-                    : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-            }
+            for (int q = 0; q < 4; ++q)
+                if ((nt0 + q) * 8 < ns)
+                    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                                 : "=r"(b0[q]), "=r"(b1[q])
+                                 : "r"(smem_u32(b + ((nt0 + q) * 8 + brow) * kStrideB + ks * 16 + bcol)));
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((nt0 + q) * 8 < ns)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                        "{%0,%1,%2,%3};\n"
+                        : "+f"(acc[q][0]), "+f"(acc[q][1]), "+f"(acc[q][2]), "+f"(acc[q][3])
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0[q]), "r"(b1[q]));
         }
         __syncthreads();
     }
