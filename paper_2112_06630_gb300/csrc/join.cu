@@ -47,7 +47,7 @@ __device__ __forceinline__ void cp_async8_w(void *dst, const void *src) {
 constexpr int kJoinWarps = 4;
 constexpr int kMergeWarps = 8;
 constexpr int kWarpMaxNv = 8;   // float32 rows of up to 32 floats take the warp kernel (measured crossover)
-constexpr int kSortMergeMin = 6; // candidates per 32-key batch from which a sort-merge beats insertions
+constexpr int kSortMergeMin = 10;  // candidates per 32-key batch from which a sort-merge beats insertions (measured: 4 slower, 8-12 flat)
 
 struct JoinLayout {
     int raw_max;      // ints for raw candidate ids
