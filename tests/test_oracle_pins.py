@@ -119,13 +119,15 @@ def test_init_uniform_chi_square():
     assert stat > chi2.ppf(0.0001, n - 1)
 
 
-def test_init_complete_graph_is_exact():
-    """K = n-1: the random initialisation already lists every other node."""
-    x = workloads.uniform(30, 4, 2)
-    st = oracle.State(x, 29, 1.0, seed=0)
+@pytest.mark.parametrize("n", [30, 65])
+def test_init_complete_graph_is_exact(n):
+    """K = n-1: the random initialisation already lists every other node
+    (also at K = 64, the widest list the GPU builds)."""
+    x = workloads.uniform(n, 4, 2)
+    st = oracle.State(x, n - 1, 1.0, seed=0)
     st.init_random()
     ids, dists, _ = st.state()
-    ei, ed = oracle.bruteforce(x, 29)
+    ei, ed = oracle.bruteforce(x, n - 1)
     assert (ids == ei).all() and (dists == ed).all()
 
 
@@ -340,12 +342,12 @@ def test_heap_sampling_build_recall():
 
 # ---------------------------------------------------------------- join ----
 
-def test_join_all_pairs_reduces_to_topk():
+@pytest.mark.parametrize("n,K", [(48, 6), (90, 48)])
+def test_join_all_pairs_reduces_to_topk(n, K):
     """Section 2 update rule fed with every pair among nodes 1..n-1 (placed in
     new[0]): each list becomes the K smallest distinct (dist, id) over its start
     entries and all other nodes except 0 -- brute force, integer data."""
     g = np.random.default_rng(1)
-    n, K = 48, 6
     xi = g.integers(0, 5, size=(n, 4))
     x = xi.astype(np.float32)
     ids0, is_new0 = workloads.random_graph(n, K, seed=3)
@@ -365,9 +367,10 @@ def test_join_all_pairs_reduces_to_topk():
     assert out["inserts"] >= out["changes"]
 
 
-def test_iterations_monotone_and_valid():
+@pytest.mark.parametrize("K", [8, 40])
+def test_iterations_monotone_and_valid(K):
     x = workloads.uniform(800, 4, 7)
-    st = oracle.State(x, 8, 0.5, seed=5)
+    st = oracle.State(x, K, 0.5, seed=5)
     st.init_random()
     prev = st.state()[1]
     for _ in range(5):
