@@ -128,10 +128,12 @@ typedef struct knng_stats {
 /*
  * One-shot K-NNG build (Section 2): random init, then up to max_iters
  * iterations of selection + calculation, stopping after the first iteration
- * whose change count is below delta * n * K; the final lists are re-ranked
- * with direct float32 difference-form distances.  rho sets the sample size
- * s = ceil(rho * K) (Section 3.1).  seed drives every random choice through a
- * counter-based SplitMix64 hash, so a build is reproducible.  Uses the legacy
+ * whose change count is below delta * n * K; the final lists carry float32
+ * difference-form distances (float32 keys hold them already; the bf16 and
+ * FP8 forms re-rank with them).  rho sets the sample size s = ceil(rho * K)
+ * (Section 3.1).  seed drives every random choice through a counter-based
+ * SplitMix64 hash, and the candidate cap drops a canonical tail, so a build
+ * is reproducible bit for bit.  Uses the legacy
  * default stream and no flags; returns when ids/dists are written.
  */
 int knng_build(const float *data, int64_t n, int d, int K, float rho, float delta,
