@@ -101,7 +101,8 @@ def test_mnist_like_n70k_d784_full_size_vs_oracle():
 
 
 def test_audio_like_n54k_d192_full_size_vs_oracle():
-    """Audio-shaped 54,387 x 192, K=20, rho=0.5 (ring kernel)."""
+    """Audio-shaped 54,387 x 192, K=20, rho=0.5 (pipelined kernel in float32,
+    ring kernel in bf16)."""
     _live_case("audio_like_n54k_d192", bf16_tol=PARITY)
 
 
@@ -115,9 +116,9 @@ def test_clustered_n100k_d16_full_size_vs_oracle():
     ("mixture_n1m_d128_rho0.7_delta0.001_iters12", 0.7, 0.001, 12),
 ])
 def test_mixture_n1m_d128_full_size_vs_stored_oracle(case, rho, delta, iters):
-    """1,000,000 x 128, 1,000 clusters, K=32 (ring join kernel): at the
-    stated parameters and at the recall-0.99 operating point the benchmark
-    times.  The bf16 form is measured beside it: its rounding of the points
+    """1,000,000 x 128, 1,000 clusters, K=32 (pipelined join kernel in
+    float32, ring kernel in bf16): at the stated parameters and at the
+    recall-0.99 operating point the benchmark times.  The bf16 form is measured beside it: its rounding of the points
     (about 1e-3 of a distance) is as large as the spacing of the 32nd and 33rd
     neighbour distances in this intrinsically 128-dimensional data, so it
     stays below float32 by more than the parity tolerance, and never more
