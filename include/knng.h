@@ -13,9 +13,12 @@
  *
  * Conventions shared by every call
  *   - Points: `data` is n x d float32, row-major, contiguous (row stride d).
- *     It may be a host pointer or a device pointer of the current device; the
- *     library tells them apart with cudaPointerGetAttributes.  Host inputs are
- *     copied to the device; host outputs are filled by a device-to-host copy.
+ *     It may be a host pointer or a device pointer of the current device (or
+ *     managed memory it can reach); the library tells them apart with
+ *     cudaPointerGetAttributes.  Host inputs are copied to the device; host
+ *     outputs are filled by a device-to-host copy; each buffer may be host or
+ *     device independently of the others.  Another device's memory, in any
+ *     argument, is refused with KNNG_ERR_INVALID_ARG before anything runs.
  *   - Output graph: ids[u*K + j] (int32) and dists[u*K + j] (float32 squared
  *     l2) hold u's j-th nearest neighbour found; each row is ascending by
  *     (dist, id), holds no self-loop and no repeated id.

@@ -35,15 +35,42 @@ int sample_size(float rho, int K) {
     return s;
 }
 
-bool is_device_ptr(const void *p) {
-    if (!p) return false;
+// Where a caller's buffer lives.  Host memory (pageable, pinned or registered)
+// goes through a device copy; memory of the current device, and managed
+// memory it can reach, is used in place; another device's memory is refused
+// before anything is launched (the kernels would fault on it, or read it over
+// the link without notice).
+enum class Where { kHost, kDevice, kForeign };
+
+Where where(const void *p) {
+    if (!p) return Where::kHost;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return Where::kHost;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return Where::kHost;
+    int dev = 0, cma = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return Where::kForeign;
+    }
+    if (cudaDeviceGetAttribute(&cma, cudaDevAttrConcurrentManagedAccess, dev) != cudaSuccess) {
+        cudaGetLastError();
+        cma = 0;
+    }
+    // test hook: classify as if another device were current (every device
+    // pointer then belongs to a foreign device), with nothing launched
+    if (std::getenv("KNNG_TEST_FOREIGN_DEVICE")) {
+        dev += 1;
+        cma = 0;
+    }
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? Where::kDevice : Where::kForeign;
+    return (a.device == dev || cma != 0) ? Where::kDevice : Where::kForeign;
 }
+
+bool is_device_ptr(const void *p) { return where(p) == Where::kDevice; }
+bool is_foreign_ptr(const void *p) { return where(p) == Where::kForeign; }
 
 // Maps a CUDA error to a return code and clears it as the thread's last error,
 // so that a failed call does not fail the next, unrelated launch check.
@@ -336,16 +363,23 @@ int ctx_stage(knng_ctx *c, const float *data) {
     const size_t bytes = sizeof(float) * c->n * c->d;
     const float *src = data;
     float *tmp = nullptr;
+    cudaError_t e = cudaSuccess;
     if (!is_device_ptr(data)) {
-        KNNG_TRY(lib_malloc((void **)&tmp, bytes, c->stream));
-        KNNG_TRY(cudaMemcpyAsync(tmp, data, bytes, cudaMemcpyHostToDevice, c->stream));
+        e = lib_malloc((void **)&tmp, bytes, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, data, bytes, cudaMemcpyHostToDevice, c->stream);
         src = tmp;
     }
-    KNNG_TRY(launch_stage(src, c->n, c->d, c->X, c->dp, c->stream));
-    c->launches++;
-    KNNG_TRY(stage_low_precision(c));
-    if (tmp) KNNG_TRY(cudaFreeAsync(tmp, c->stream));
-    return KNNG_OK;
+    if (e == cudaSuccess) e = launch_stage(src, c->n, c->d, c->X, c->dp, c->stream);
+    if (e == cudaSuccess) {
+        c->launches++;
+        e = stage_low_precision(c);
+    }
+    // the staging copy is freed on every path, a failed one included
+    if (tmp) {
+        const cudaError_t f = cudaFreeAsync(tmp, c->stream);
+        if (e == cudaSuccess) e = f;
+    }
+    return cuda_code(e);
 }
 
 // data == nullptr: allocate only (the batched build stages its data sets)
@@ -355,6 +389,7 @@ int ctx_create(knng_ctx **out, const float *data, int64_t n, int d, int K, float
     *out = nullptr;
     int rc = check_args(n, d, K, rho, delta);
     if (rc) return rc;
+    if (data && is_foreign_ptr(data)) return KNNG_ERR_INVALID_ARG;
     // lists of more than 32 keys: float32 keys with turbosampling only (the
     // low-precision forms resolve keys per id, and heap selection keeps its
     // lists one per lane)
@@ -653,7 +688,9 @@ int knng_init(knng_ctx **out, const float *data, int64_t n, int d, int K, float 
 int knng_init_from_graph(knng_ctx **out, const float *data, int64_t n, int d, int K, float rho, float delta,
                          uint64_t seed, uint32_t flags, void *stream, const int32_t *ids, const uint8_t *is_new,
                          int iter) {
+    if (out) *out = nullptr;
     if (!data || !ids || !is_new || iter < 0) return KNNG_ERR_INVALID_ARG;
+    if (is_foreign_ptr(ids) || is_foreign_ptr(is_new)) return KNNG_ERR_INVALID_ARG;
     int rc = ctx_create(out, data, n, d, K, rho, delta, seed, flags, stream);
     if (rc) return rc;
     knng_ctx *c = *out;
@@ -757,6 +794,9 @@ int knng_reorder(knng_ctx *c) {
 
 int knng_get(knng_ctx *c, int32_t *ids, float *dists) {
     if (!c || !ids || !dists) return KNNG_ERR_INVALID_ARG;
+    if (is_foreign_ptr(ids) || is_foreign_ptr(dists)) return KNNG_ERR_INVALID_ARG;
+    // both on the device: written in place; otherwise through a device buffer
+    // and copied out with the direction taken from each pointer
     const bool dev_out = is_device_ptr(ids) && is_device_ptr(dists);
     const size_t ib = sizeof(int32_t) * c->n * c->K, db = sizeof(float) * c->n * c->K;
     int32_t *oi = ids;
@@ -776,8 +816,8 @@ int knng_get(knng_ctx *c, int32_t *ids, float *dists) {
                            od, c->stream));
     c->launches++;
     if (!dev_out) {
-        KNNG_TRY(cudaMemcpyAsync(ids, oi, ib, cudaMemcpyDeviceToHost, c->stream));
-        KNNG_TRY(cudaMemcpyAsync(dists, od, db, cudaMemcpyDeviceToHost, c->stream));
+        KNNG_TRY(cudaMemcpyAsync(ids, oi, ib, cudaMemcpyDefault, c->stream));
+        KNNG_TRY(cudaMemcpyAsync(dists, od, db, cudaMemcpyDefault, c->stream));
         KNNG_TRY(cudaFreeAsync(tmp, c->stream));
         return ctx_check(c);
     }
@@ -935,6 +975,7 @@ int knng_destroy(knng_ctx *c) {
 int knng_build_ex(const float *data, int64_t n, int d, int K, float rho, float delta, int max_iters, uint64_t seed,
                   uint32_t flags, void *stream, int32_t *ids, float *dists, knng_stats *stats) {
     if (max_iters < 0 || max_iters > kMaxItersArg || !ids || !dists) return KNNG_ERR_INVALID_ARG;
+    if (is_foreign_ptr(ids) || is_foreign_ptr(dists)) return KNNG_ERR_INVALID_ARG;
     knng_ctx *c = nullptr;
     int rc = knng_init(&c, data, n, d, K, rho, delta, seed, flags, stream);
     if (rc) return rc;
@@ -1110,8 +1151,11 @@ int knng_build_batched(const knng_desc *descs, int count, int K, float rho, floa
                        uint64_t seed, uint32_t flags, void *stream, knng_stats *stats) {
     if (!descs || count < 1 || max_iters < 0 || max_iters > kMaxItersArg) return KNNG_ERR_INVALID_ARG;
     if (flags & (KNNG_FLAG_REORDER | KNNG_FLAG_REORDER_B)) return KNNG_ERR_UNSUPPORTED;
-    for (int b = 0; b < count; ++b)
-        if (descs[b].d < 1) return KNNG_ERR_INVALID_ARG;
+    for (int b = 0; b < count; ++b) {
+        const knng_desc &e = descs[b];
+        if (e.d < 1 || is_foreign_ptr(e.data) || is_foreign_ptr(e.ids) || is_foreign_ptr(e.dists))
+            return KNNG_ERR_INVALID_ARG;
+    }
     // one batched build per row-width class, widest last
     std::vector<int> cls(count);
     for (int b = 0; b < count; ++b) cls[b] = width_class(descs[b].d);
@@ -1144,6 +1188,7 @@ int knng_build_batched_ex(const knng_desc_ex *descs, int count, uint32_t flags, 
         if (!e.data || !e.ids || !e.dists || e.n < 2 || e.d < 1 || e.K < 1 || !(e.rho > 0.f && e.rho <= 1.f) ||
             !(e.delta >= 0.f) || e.max_iters < 0 || e.max_iters > kMaxItersArg)
             return KNNG_ERR_INVALID_ARG;
+        if (is_foreign_ptr(e.data) || is_foreign_ptr(e.ids) || is_foreign_ptr(e.dists)) return KNNG_ERR_INVALID_ARG;
         if (e.K > kMaxK) return KNNG_ERR_UNSUPPORTED;
         if (e.K > kLaneK && (flags & (KNNG_FLAG_BF16 | KNNG_FLAG_FP8 | KNNG_FLAG_HEAP_SAMPLING)))
             return KNNG_ERR_UNSUPPORTED;
@@ -1216,6 +1261,8 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
     if (K > kMaxK) return KNNG_ERR_UNSUPPORTED;
     if (!rows) nq = n;
     if (nq < 1) return KNNG_ERR_INVALID_ARG;
+    if (is_foreign_ptr(data) || is_foreign_ptr(ids) || is_foreign_ptr(dists) || is_foreign_ptr(rows))
+        return KNNG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int dp = (d + 3) & ~3;
     const size_t xb = align256(sizeof(float) * n * dp), rb = rows ? align256(sizeof(int64_t) * nq) : 0;
@@ -1282,8 +1329,8 @@ int knng_bruteforce(const float *data, int64_t n, int d, int K, const int64_t *r
     }
     if (e == cudaSuccess && !tc) e = launch_bruteforce(X, n, dp, K, rows_d, nq, oi, od, s, part, S);
     if (e == cudaSuccess && !dev_out) {
-        e = cudaMemcpyAsync(ids, oi, sizeof(int32_t) * nq * K, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dists, od, sizeof(float) * nq * K, cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(ids, oi, sizeof(int32_t) * nq * K, cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dists, od, sizeof(float) * nq * K, cudaMemcpyDefault, s);
     }
     if (staged) cudaFreeAsync(staged, s);
     cudaFreeAsync(tmp, s);

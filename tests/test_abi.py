@@ -91,6 +91,16 @@ def test_null_pointers_rejected(lib):
     assert lib.knng_init(ctypes.byref(h), None, 10, 4, 3, 0.5, 0.0, 0, 0, None) == -1
     assert lib.knng_iterate(None, None) == -1
     assert lib.knng_destroy(None) == 0
+    # a refused call leaves no stale context behind: *out is NULL on error
+    x = np.zeros((10, 4), np.float32)
+    ids = np.zeros((10, 3), np.int32)
+    flags = np.zeros((10, 3), np.uint8)
+    for bad in [(None, ids, flags, 0), (x, None, flags, 0), (x, ids, None, 0), (x, ids, flags, -1)]:
+        h = ctypes.c_void_p(0x1234)
+        ptrs = [a.ctypes.data if a is not None else None for a in bad[:3]]
+        assert lib.knng_init_from_graph(ctypes.byref(h), ptrs[0], 10, 4, 3, 0.5, 0.0, 0, 0, None, ptrs[1], ptrs[2],
+                                        bad[3]) == -1
+        assert h.value is None
 
 
 def test_header_compiles_as_c11(tmp_path):
