@@ -1,6 +1,7 @@
 """The benchmark's multi-rank plumbing on CPU (gloo, world size 2): the
 step time is the maximum over ranks, the barrier joins every rank, and under
-a multi-rank launch only rank 0 runs and prints the reference arm."""
+a multi-rank launch only rank 0 runs and prints the reference arm, whose
+line carries the contract's keys."""
 import os
 import socket
 import subprocess
@@ -53,3 +54,28 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_line_on_rank_zero():
+    """Rank 0 (or a plain launch) prints one JSON line with the contract's
+    keys: impl "reference", the oracle's time as value, a cpu_baseline that
+    describes the run, and an e2e with no host-device bytes."""
+    import json
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "uniform_n2k_d8", "--steps", "2", "--warmup", "1"], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    lines = r.stdout.strip().splitlines()
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["higher_is_better"] is False and line["value"] > 0
+    assert line["config"]["workload"] == "uniform_n2k_d8" and line["config"]["n"] == 2000
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
