@@ -875,9 +875,11 @@ def _workload(args):
 def run_reference(args):
     """The reference arm: the CPU oracle on the same workload and timed point,
     one thread.  Set-up (untimed, once): the oracle's random init and the
-    selection step of iteration 1 on the whole point set.  Each step then
-    times the calculation step of the next block of nodes (about two seconds
-    of it) and scales it to one whole build by distance evaluations, so the
+    selection step of iteration 1 on the whole point set.  Where a whole
+    build takes about two seconds or less (judged from the first block of
+    nodes), each step times one whole build.  Otherwise each step times the
+    calculation step of the next block of nodes (about two seconds of it) and
+    scales it to one whole build by distance evaluations, so the
     --steps/--warmup run stays within a few minutes."""
     ws, rank, local = _dist()
     if rank != 0:
@@ -895,7 +897,22 @@ def run_reference(args):
         E = sum(len(a) * (len(a) - 1) // 2 + len(a) * len(b) for a, b in zip(*s.samples())) * op.max_iters
         src = "iteration 1's evaluations times the iteration cap (no stored count for this point)"
     chunk = max(16, op.n // 5000)
-    u0, vals, tot_t, tot_e = 0, [], 0.0, 0
+    t0 = time.perf_counter()
+    r = s.join_range(0, chunk)
+    probe_s = (time.perf_counter() - t0) * E / max(1, r["evals"])
+    if probe_s <= 2.0:
+        s.close()
+        vals = []
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            oracle.build_knng(x, op.K, op.rho, op.delta, op.max_iters, seed=0)
+            if i >= args.warmup:
+                vals.append(time.perf_counter() - t0)
+        _print_reference(ws, args, w, wname, op, sum(vals) / len(vals),
+                         "per step, one whole build of the workload on one thread")
+        return
+    # the probe block was the first of the sequence: carry on after it
+    u0, vals = chunk, []
     for i in range(args.warmup + args.steps):
         t, ev = 0.0, 0
         while t < 2.0:
@@ -912,12 +929,14 @@ def run_reference(args):
             u0 += chunk
         if i >= args.warmup:
             vals.append(t * E / max(1, ev))
-            tot_t += t
-            tot_e += ev
     s.close()
-    v = sum(vals) / len(vals)
-    sample = (f"per step, the calculation step of iteration 1 for about 2 s of nodes on one thread, scaled to the "
-              f"{E} distance evaluations of a whole build ({src})")
+    _print_reference(ws, args, w, wname, op, sum(vals) / len(vals),
+                     f"per step, the calculation step of iteration 1 for about 2 s of nodes on one thread, scaled "
+                     f"to the {E} distance evaluations of a whole build ({src})")
+
+
+def _print_reference(ws, args, w, wname, op, v, sample):
+    """The reference arm's JSON line: the oracle's seconds per build v."""
     line = {
         "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1),
